@@ -1,0 +1,586 @@
+/*
+ * oracle39.c -- plain, slow FP64 CPU oracle of the 13-moment guided-equilibrium
+ * double-distribution-function lattice Boltzmann step on D3Q39
+ * (Latt, Coreixas, Beny, Parmigiani, "Efficient supersonic flows through
+ * high-order guided equilibrium with lattice Boltzmann", arXiv:1910.13515).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA path is
+ * checked against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it.  It shares no code, table or header with
+ * the CUDA library; the product path never calls it.
+ *
+ * Every function follows the paper's algorithm in the paper's order, written
+ * for a reader checking it by eye: no blocking, no fusion, no symmetry tricks.
+ * Readings of garbled or silent passages are marked "reading:".
+ *
+ * Layout (this file's own choice): populations f[cell*39 + i], g[cell*39 + i];
+ * multipliers lam[cell*13 + k]; cell = x + nx*(y + ny*z).
+ * Mask codes: 0 fluid, 1 solid (half-way bounce-back), 2 freestream
+ * (equilibrium at the far-field state), 3 outflow (zero-gradient copy along x).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 39   /* velocities of D3Q39 (Sec. 3) */
+#define NM 13  /* constraints / multipliers (Eq. 13constraints) */
+#define DIM 3
+
+enum { M_FLUID = 0, M_SOLID = 1, M_FREE = 2, M_OUT = 3 };
+
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t periodic[3];
+  double gamma;        /* heat-capacity ratio; C_v = 1/(gamma-1) (Sec. 2) */
+  double tau;          /* BGK relaxation time, tau_f = tau_g (Pr = 1, Sec. 3) */
+  int32_t kn_sensor;   /* 1: tau(eps) = tau*alpha(eps) (Eq. alpha) */
+  double newton_tol;   /* stop when max |G_k| < tol (Sec. 5 step table) */
+  int32_t newton_maxit;
+  int32_t newton_min_upd; /* reading: at least this many updates per solve */
+  double rho_inf, u_inf[3], T_inf; /* far-field state for freestream cells */
+} o39_params;
+
+typedef struct {
+  int64_t fluid_cells;
+  int64_t failed_cells;
+  int64_t newton_updates;  /* summed over fluid cells */
+  int64_t hist[32];        /* cells by number of Newton updates (clipped) */
+  int64_t eps_hist[4];     /* cells by alpha branch */
+} o39_stats;
+
+/* ---------------------------------------------------------------------- */
+/* Lattice (Sec. 3): D3Q39 = Shan's E^39_{3,7}: (0,0,0), (1,0,0)_FS,
+ * (+-1,+-1,+-1), (2,0,0)_FS, (2,2,0)_FS, (3,0,0)_FS.  "FS" = all sign and
+ * axis permutations.  Enumerated over [-3,3]^3 in lexicographic order.      */
+static int VEL[Q][DIM];
+static int OPP[Q];
+static double WGT[Q];
+static int lattice_ready = 0;
+
+static int shell_of(int a, int b, int c) {
+  /* sorted absolute components identify the shell; -1 = not in D3Q39 */
+  int v[3] = {abs(a), abs(b), abs(c)};
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j)
+      if (v[j] < v[i]) { int t = v[i]; v[i] = v[j]; v[j] = t; }
+  if (v[0] == 0 && v[1] == 0 && v[2] == 0) return 0;
+  if (v[0] == 0 && v[1] == 0 && v[2] == 1) return 1;
+  if (v[0] == 1 && v[1] == 1 && v[2] == 1) return 2;
+  if (v[0] == 0 && v[1] == 0 && v[2] == 2) return 3;
+  if (v[0] == 0 && v[1] == 2 && v[2] == 2) return 4;
+  if (v[0] == 0 && v[1] == 0 && v[2] == 3) return 5;
+  return -1;
+}
+
+/* Shan's quadrature weights for E^39_{3,7}, per shell.  The method itself is
+ * quadrature-free and never uses them (Sec. 2, after Eq. constraints); they
+ * are exported as lattice metadata only. */
+static const double SHELL_W[6] = {1.0 / 12.0, 1.0 / 12.0, 1.0 / 27.0,
+                                  2.0 / 135.0, 1.0 / 432.0, 1.0 / 1620.0};
+
+static void build_lattice(void) {
+  if (lattice_ready) return;
+  int n = 0;
+  for (int a = -3; a <= 3; ++a)
+    for (int b = -3; b <= 3; ++b)
+      for (int c = -3; c <= 3; ++c) {
+        int s = shell_of(a, b, c);
+        if (s < 0) continue;
+        VEL[n][0] = a; VEL[n][1] = b; VEL[n][2] = c;
+        WGT[n] = SHELL_W[s];
+        ++n;
+      }
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j < Q; ++j)
+      if (VEL[j][0] == -VEL[i][0] && VEL[j][1] == -VEL[i][1] && VEL[j][2] == -VEL[i][2])
+        OPP[i] = j;
+  lattice_ready = (n == Q);
+}
+
+int o39_lattice(int32_t *vel, double *w, int32_t *opp) {
+  build_lattice();
+  for (int i = 0; i < Q; ++i) {
+    for (int d = 0; d < DIM; ++d) vel[3 * i + d] = VEL[i][d];
+    w[i] = WGT[i];
+    opp[i] = OPP[i];
+  }
+  return lattice_ready ? Q : -1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Moment basis of Eq. (discrete-equilibrium): the 13 monomials whose
+ * multipliers appear in the exponent,
+ *   phi = [1, xi_x, xi_y, xi_z, xi_x^2, xi_y^2, xi_z^2, xi_x xi_y, xi_x xi_z,
+ *          xi_y xi_z, xi_x |xi|^2, xi_y |xi|^2, xi_z |xi|^2].
+ * The off-diagonal entries of the symmetric tensor lambda_2 appear twice in
+ * lambda_2:xi xi; here their sum is one multiplier (same function space). */
+void o39_basis(const int32_t *xi, double *phi) {
+  double x = xi[0], y = xi[1], z = xi[2];
+  double s = x * x + y * y + z * z;
+  phi[0] = 1.0;
+  phi[1] = x; phi[2] = y; phi[3] = z;
+  phi[4] = x * x; phi[5] = y * y; phi[6] = z * z;
+  phi[7] = x * y; phi[8] = x * z; phi[9] = y * z;
+  phi[10] = x * s; phi[11] = y * s; phi[12] = z * s;
+}
+
+static void basis_i(int i, double *phi) {
+  int32_t xi[3] = {VEL[i][0], VEL[i][1], VEL[i][2]};
+  o39_basis(xi, phi);
+}
+
+/* Targets, Eq. (13constraints), divided by rho:
+ *   M0 = 1; M1_a = u_a; M2_ab = u_a u_b + T delta_ab;
+ *   M3_a = sum_b M3_abb = u_a (u^2 + (D+2) T).
+ * reading: the printed right-hand side "(2 rho E^tr + 2 rho T) u_a" with
+ * "E^tr = D T + rho u^2" is dimensionally garbled; the contracted third
+ * moment of the Maxwell-Boltzmann distribution (Eq. EqMomentsTensor,
+ * contracted over beta = gamma) is rho u_a (u^2 + (D+2) T), which equals the
+ * printed form for rho E^tr = rho u^2 / 2 + D rho T / 2. */
+void o39_targets(const double *u, double T, double *m) {
+  double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  m[0] = 1.0;
+  m[1] = u[0]; m[2] = u[1]; m[3] = u[2];
+  m[4] = u[0] * u[0] + T; m[5] = u[1] * u[1] + T; m[6] = u[2] * u[2] + T;
+  m[7] = u[0] * u[1]; m[8] = u[0] * u[2]; m[9] = u[1] * u[2];
+  m[10] = u[0] * (u2 + (DIM + 2) * T);
+  m[11] = u[1] * (u2 + (DIM + 2) * T);
+  m[12] = u[2] * (u2 + (DIM + 2) * T);
+}
+
+/* Normalised exponential equilibrium, Eq. (discrete-equilibrium) / rho:
+ *   F_i = exp(sum_k lam_k phi_k(xi_i)),  f_i^eq = rho F_i. */
+void o39_feq_norm(const double *lam, double *F) {
+  build_lattice();
+  for (int i = 0; i < Q; ++i) {
+    double phi[NM];
+    basis_i(i, phi);
+    double e = 0.0;
+    for (int k = 0; k < NM; ++k) e += lam[k] * phi[k];
+    F[i] = exp(e);
+  }
+}
+
+/* Constraint residual, Eq. (constraints): G_k = sum_i F_i phi_k(xi_i) - m_k. */
+static void residual_from_F(const double *F, const double *m, double *G) {
+  for (int k = 0; k < NM; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      double phi[NM];
+      basis_i(i, phi);
+      s += F[i] * phi[k];
+    }
+    G[k] = s - m[k];
+  }
+}
+
+void o39_residual(const double *lam, const double *m, double *G) {
+  double F[Q];
+  o39_feq_norm(lam, F);
+  residual_from_F(F, m, G);
+}
+
+/* Jacobian of G w.r.t. lambda (Sec. 5 step table): J_kl = sum_i F_i phi_k phi_l. */
+static void jacobian_from_F(const double *F, double *J) {
+  for (int k = 0; k < NM; ++k)
+    for (int l = 0; l < NM; ++l) {
+      double s = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        double phi[NM];
+        basis_i(i, phi);
+        s += F[i] * phi[k] * phi[l];
+      }
+      J[k * NM + l] = s;
+    }
+}
+
+void o39_jacobian(const double *lam, double *J) {
+  double F[Q];
+  o39_feq_norm(lam, F);
+  jacobian_from_F(F, J);
+}
+
+/* "Compute inverse of J" (Sec. 5 step table): textbook Gauss-Jordan
+ * elimination with partial pivoting.  Returns 0, or -1 if singular. */
+int o39_invert(const double *Jin, double *Jinv) {
+  double a[NM][2 * NM];
+  for (int r = 0; r < NM; ++r)
+    for (int c = 0; c < NM; ++c) {
+      a[r][c] = Jin[r * NM + c];
+      a[r][NM + c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < NM; ++c) {
+    int p = c;
+    for (int r = c + 1; r < NM; ++r)
+      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
+    if (!(fabs(a[p][c]) > 0.0)) return -1;
+    if (p != c)
+      for (int k = 0; k < 2 * NM; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+    double piv = a[c][c];
+    for (int k = 0; k < 2 * NM; ++k) a[c][k] /= piv;
+    for (int r = 0; r < NM; ++r) {
+      if (r == c) continue;
+      double fct = a[r][c];
+      if (fct == 0.0) continue;
+      for (int k = 0; k < 2 * NM; ++k) a[r][k] -= fct * a[c][k];
+    }
+  }
+  for (int r = 0; r < NM; ++r)
+    for (int c = 0; c < NM; ++c) Jinv[r * NM + c] = a[r][NM + c];
+  return 0;
+}
+
+static double maxabs(const double *v) {
+  double r = 0.0;
+  for (int k = 0; k < NM; ++k) {
+    double a = fabs(v[k]);
+    if (!(a <= r)) r = a; /* NaN propagates */
+  }
+  return r;
+}
+
+static double sumsq(const double *v) {
+  double s = 0.0;
+  for (int k = 0; k < NM; ++k) s += v[k] * v[k];
+  return s;
+}
+
+/* Gaussian starting point for a cold start.
+ * reading (the paper only says lambda is inherited from the previous step):
+ * lam_1 = u/T, diagonal lam_2 = -1/(2T), everything else 0, and lam_0
+ * normalises sum_i F_i = 1 -- the discrete Maxwellian exp(-(xi-u)^2/(2T)). */
+void o39_gaussian_guess(const double *u, double T, double *lam) {
+  build_lattice();
+  for (int k = 0; k < NM; ++k) lam[k] = 0.0;
+  lam[1] = u[0] / T; lam[2] = u[1] / T; lam[3] = u[2] / T;
+  lam[4] = lam[5] = lam[6] = -0.5 / T;
+  double F[Q];
+  o39_feq_norm(lam, F);
+  double s = 0.0;
+  for (int i = 0; i < Q; ++i) s += F[i];
+  lam[0] = -log(s);
+}
+
+#define LS_MAX 30
+
+/* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
+ * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
+ *          lam <- lam - J^{-1} G } until max|G| < tol.
+ * reading (stopping and damping are not specified beyond "norm below 1e-12"):
+ *  - at least `min_upd` updates are taken, so a converged warm start is still
+ *    polished by one full step;
+ *  - a solve that lands between tol/100 and tol (above the round-off floor of
+ *    the residual) takes one more full "polishing" step from there; with
+ *    quadratic convergence that step ends at round-off, so the collision
+ *    conserves mass, momentum and energy to round-off;
+ *  - while not converged, the step is halved until ||G||_2 decreases
+ *    (backtracking), which keeps a cold start from overflowing;
+ *  - more than `maxit` updates, or no decrease within LS_MAX halvings, is a
+ *    failure (return 1; lam keeps its last accepted value).
+ * On return F holds exp(Phi lam) at the returned lam. */
+int o39_newton(const double *m, double *lam, double tol, int maxit, int min_upd,
+               int *n_upd_out, double *F) {
+  build_lattice();
+  double G[NM];
+  o39_feq_norm(lam, F);
+  residual_from_F(F, m, G);
+  int n_upd = 0, status = 0, polished = 0;
+  for (;;) {
+    double r = maxabs(G);
+    if (n_upd >= min_upd && r < tol && (r < 1e-2 * tol || polished)) break;
+    if (n_upd >= maxit) { status = 1; break; }
+    double J[NM * NM], Ji[NM * NM], d[NM];
+    jacobian_from_F(F, J);
+    if (o39_invert(J, Ji) != 0) { status = 1; break; }
+    for (int k = 0; k < NM; ++k) {
+      double s = 0.0;
+      for (int l = 0; l < NM; ++l) s += Ji[k * NM + l] * G[l];
+      d[k] = s;
+    }
+    double lt[NM], Ft[Q], Gt[NM];
+    polished = (r < tol);
+    if (polished) { /* polishing step: always full */
+      for (int k = 0; k < NM; ++k) lt[k] = lam[k] - d[k];
+      o39_feq_norm(lt, Ft);
+      residual_from_F(Ft, m, Gt);
+    } else {
+      double s0 = sumsq(G), t = 1.0;
+      int ok = 0;
+      for (int ls = 0; ls <= LS_MAX; ++ls) {
+        for (int k = 0; k < NM; ++k) lt[k] = lam[k] - t * d[k];
+        o39_feq_norm(lt, Ft);
+        residual_from_F(Ft, m, Gt);
+        if (sumsq(Gt) < s0) { ok = 1; break; }
+        t *= 0.5;
+      }
+      if (!ok) { status = 1; break; }
+    }
+    memcpy(lam, lt, sizeof lt);
+    memcpy(F, Ft, sizeof Ft);
+    memcpy(G, Gt, sizeof Gt);
+    ++n_upd;
+  }
+  if (n_upd_out) *n_upd_out = n_upd;
+  return status;
+}
+
+/* alpha(eps), Eq. (alpha): 1 below 1e-2, 1.05 on [1e-2,1e-1), 1.35 on
+ * [1e-1,1), and 1/tau from 1 upward (then tau*alpha = 1: h* = h^eq). */
+double o39_alpha(double eps, double tau) {
+  if (eps < 1e-2) return 1.0;
+  if (eps < 1e-1) return 1.05;
+  if (eps < 1.0) return 1.35;
+  return 1.0 / tau;
+}
+
+static int alpha_branch(double eps) {
+  if (eps < 1e-2) return 0;
+  if (eps < 1e-1) return 1;
+  if (eps < 1.0) return 2;
+  return 3;
+}
+
+/* Macroscopic variables of one cell (Sec. 3, first collision step):
+ * rho = sum f, rho u = sum f xi, and T from the total energy
+ *   sum f |xi|^2 + sum g = rho u^2 + 2 C_v rho T    (E = u^2/2 + C_v T, Sec. 2).
+ * reading: T is taken from the total energy of both populations, which is
+ * what makes g^eq = (2C_v - D) T f^eq conserve energy. */
+void o39_cell_macros(const o39_params *p, const double *f, const double *g,
+                     double *rho_out, double *u_out, double *T_out) {
+  build_lattice();
+  double cv = 1.0 / (p->gamma - 1.0);
+  double rho = 0.0, j[3] = {0, 0, 0}, e2 = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    for (int d = 0; d < DIM; ++d) j[d] += f[i] * VEL[i][d];
+    double c2 = VEL[i][0] * VEL[i][0] + VEL[i][1] * VEL[i][1] + VEL[i][2] * VEL[i][2];
+    e2 += f[i] * c2 + g[i];
+  }
+  double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+  double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  *rho_out = rho;
+  for (int d = 0; d < DIM; ++d) u_out[d] = u[d];
+  *T_out = (e2 - rho * u2) / (2.0 * cv * rho);
+}
+
+/* One BGK collision of one fluid cell (Sec. 3 and Eq. DeltaAvg / alpha):
+ * macros -> MB targets -> Newton (warm start lam) -> f^eq, g^eq = (2C_v-D) T f^eq
+ * -> eps, alpha -> h* = h - (h - h^eq)/(tau alpha) for h = f and h = g.
+ * reading: eps uses f only and the same alpha relaxes f and g (Pr = 1).
+ * In place on f, g, lam.  Returns the Newton status. */
+int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam,
+                     int *n_upd, double *eps_out, double *alpha_out) {
+  build_lattice();
+  double cv = 1.0 / (p->gamma - 1.0);
+  double rho, u[3], T;
+  o39_cell_macros(p, f, g, &rho, u, &T);
+  double m[NM], F[Q];
+  o39_targets(u, T, m);
+  int st = o39_newton(m, lam, p->newton_tol, p->newton_maxit, p->newton_min_upd, n_upd, F);
+  double feq[Q], geq[Q];
+  for (int i = 0; i < Q; ++i) {
+    feq[i] = rho * F[i];
+    geq[i] = (2.0 * cv - DIM) * T * feq[i];
+  }
+  double eps = 0.0;
+  for (int i = 0; i < Q; ++i) eps += fabs(f[i] - feq[i]) / feq[i];
+  eps /= Q;
+  double alpha = p->kn_sensor ? o39_alpha(eps, p->tau) : 1.0;
+  double tau_eff = p->tau * alpha;
+  for (int i = 0; i < Q; ++i) {
+    f[i] = f[i] - (f[i] - feq[i]) / tau_eff;
+    g[i] = g[i] - (g[i] - geq[i]) / tau_eff;
+  }
+  if (eps_out) *eps_out = eps;
+  if (alpha_out) *alpha_out = alpha;
+  return st;
+}
+
+/* Equilibrium populations and multipliers of a state (rho, u, T) from the
+ * Gaussian cold start (used for initial conditions and far-field cells). */
+int o39_equilibrium(const o39_params *p, double rho, const double *u, double T,
+                    double *feq, double *geq, double *lam, int maxit) {
+  build_lattice();
+  double cv = 1.0 / (p->gamma - 1.0);
+  double m[NM], F[Q];
+  o39_targets(u, T, m);
+  o39_gaussian_guess(u, T, lam);
+  int nu = 0;
+  int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, &nu, F);
+  for (int i = 0; i < Q; ++i) {
+    feq[i] = rho * F[i];
+    geq[i] = (2.0 * cv - DIM) * T * feq[i];
+  }
+  return st;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Lattice-level operations. */
+
+static int64_t cell_index(const o39_params *p, int x, int y, int z) {
+  return (int64_t)x + (int64_t)p->nx * ((int64_t)y + (int64_t)p->ny * z);
+}
+
+static int wrap(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+/* Initial condition: every fluid cell at its local equilibrium f^eq(rho,u,T),
+ * g^eq, with lam from a cold-start Newton; other cells hold zeros.
+ * u is given as three planes u[d*N + cell].  Returns the failed-cell count. */
+int64_t o39_init(const o39_params *p, const uint8_t *mask, const double *rho,
+                 const double *u, const double *T, double *f, double *g,
+                 double *lam, int maxit) {
+  build_lattice();
+  int64_t N = (int64_t)p->nx * p->ny * p->nz;
+  int64_t failed = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : failed)
+  for (int64_t c = 0; c < N; ++c) {
+    if (mask[c] != M_FLUID) {
+      for (int i = 0; i < Q; ++i) { f[c * Q + i] = 0.0; g[c * Q + i] = 0.0; }
+      for (int k = 0; k < NM; ++k) lam[c * NM + k] = 0.0;
+      continue;
+    }
+    double uc[3] = {u[c], u[N + c], u[2 * N + c]};
+    failed += o39_equilibrium(p, rho[c], uc, T[c], f + c * Q, g + c * Q, lam + c * NM, maxit);
+  }
+  return failed;
+}
+
+/* Post-collision value of a non-fluid source cell s in direction i.
+ * reading (the paper gives the boundary kinds but not their reach on a
+ * lattice with shifts up to 3): freestream cells hold h^eq at the far-field
+ * state every step; an outflow cell copies the post-collision populations of
+ * the cell reached by clamping its x into [3, nx-4] (zero gradient along x,
+ * "first-order Neumann"). */
+static double ghost_post(const o39_params *p, const uint8_t *mask, const double *post,
+                         const double *heq_inf, int x, int y, int z, int i) {
+  int64_t s = cell_index(p, x, y, z);
+  if (mask[s] == M_FREE) return heq_inf[i];
+  /* outflow */
+  int xc = x < 3 ? 3 : (x > p->nx - 4 ? p->nx - 4 : x);
+  int64_t c = cell_index(p, xc, y, z);
+  if (mask[c] == M_FREE) return heq_inf[i];
+  return post[c * Q + i];
+}
+
+/* Streaming, Eq. after Sec. 3: h_i(x + xi_i, t+1) = h*_i(x, t), written as a
+ * pull: h_i(x, t+1) = h*_i(x - xi_i), with periodic wrap of the index; if
+ * the source x - xi_i is solid, half-way bounce-back returns the population
+ * that left x towards it: h_i(x, t+1) = h*_opp(i)(x).
+ * reading (destination rule): only the end point of a link is tested; cells
+ * the link passes over are not.  Only fluid cells are written. */
+void o39_stream(const o39_params *p, const uint8_t *mask, const double *fpost,
+                const double *gpost, const double *feq_inf, const double *geq_inf,
+                double *fout, double *gout) {
+  build_lattice();
+  int nx = p->nx, ny = p->ny, nz = p->nz;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        int64_t c = cell_index(p, x, y, z);
+        if (mask[c] != M_FLUID) continue;
+        for (int i = 0; i < Q; ++i) {
+          int sx = wrap(x - VEL[i][0], nx), sy = wrap(y - VEL[i][1], ny),
+              sz = wrap(z - VEL[i][2], nz);
+          int64_t s = cell_index(p, sx, sy, sz);
+          if (mask[s] == M_SOLID) {
+            fout[c * Q + i] = fpost[c * Q + OPP[i]];
+            gout[c * Q + i] = gpost[c * Q + OPP[i]];
+          } else if (mask[s] == M_FLUID) {
+            fout[c * Q + i] = fpost[s * Q + i];
+            gout[c * Q + i] = gpost[s * Q + i];
+          } else {
+            fout[c * Q + i] = ghost_post(p, mask, fpost, feq_inf, sx, sy, sz, i);
+            gout[c * Q + i] = ghost_post(p, mask, gpost, geq_inf, sx, sy, sz, i);
+          }
+        }
+      }
+}
+
+/* nsteps full time steps: collide every fluid cell, then stream (pull) from
+ * the post-collision array back into f, g.  Returns failed Newton solves. */
+int64_t o39_step(const o39_params *p, const uint8_t *mask, double *f, double *g,
+                 double *lam, int nsteps, o39_stats *st) {
+  build_lattice();
+  int64_t N = (int64_t)p->nx * p->ny * p->nz;
+  double *fp = (double *)malloc(sizeof(double) * N * Q);
+  double *gp = (double *)malloc(sizeof(double) * N * Q);
+  double feq_inf[Q], geq_inf[Q], lam_inf[NM];
+  o39_equilibrium(p, p->rho_inf, p->u_inf, p->T_inf, feq_inf, geq_inf, lam_inf, 200);
+  int64_t failed_total = 0;
+  for (int t = 0; t < nsteps; ++t) {
+    int64_t failed = 0, upd = 0, fluid = 0;
+    int64_t hist[32] = {0}, ehist[4] = {0};
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : failed, upd, fluid)
+    for (int64_t c = 0; c < N; ++c) {
+      for (int i = 0; i < Q; ++i) { fp[c * Q + i] = f[c * Q + i]; gp[c * Q + i] = g[c * Q + i]; }
+      if (mask[c] != M_FLUID) continue;
+      int nu = 0;
+      double eps, alpha;
+      failed += o39_collide_cell(p, fp + c * Q, gp + c * Q, lam + c * NM, &nu, &eps, &alpha);
+      upd += nu;
+      fluid += 1;
+      int b = nu < 31 ? nu : 31;
+      int eb = alpha_branch(eps);
+#pragma omp atomic
+      hist[b] += 1;
+#pragma omp atomic
+      ehist[eb] += 1;
+    }
+    o39_stream(p, mask, fp, gp, feq_inf, geq_inf, f, g);
+    failed_total += failed;
+    if (st) {
+      st->fluid_cells = fluid;
+      st->failed_cells += failed;
+      st->newton_updates += upd;
+      for (int k = 0; k < 32; ++k) st->hist[k] += hist[k];
+      for (int k = 0; k < 4; ++k) st->eps_hist[k] += ehist[k];
+    }
+  }
+  free(fp);
+  free(gp);
+  return failed_total;
+}
+
+/* Macroscopic fields of the pre-collision state: rho, u (3 planes), T and
+ * p = rho T (ideal gas in lattice units).  Non-fluid cells read as 0. */
+void o39_macros(const o39_params *p, const uint8_t *mask, const double *f,
+                const double *g, double *rho, double *u, double *T, double *pr) {
+  build_lattice();
+  int64_t N = (int64_t)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < N; ++c) {
+    if (mask[c] != M_FLUID) {
+      rho[c] = 0; u[c] = 0; u[N + c] = 0; u[2 * N + c] = 0; T[c] = 0; pr[c] = 0;
+      continue;
+    }
+    double r, uc[3], Tc;
+    o39_cell_macros(p, f + c * Q, g + c * Q, &r, uc, &Tc);
+    rho[c] = r; u[c] = uc[0]; u[N + c] = uc[1]; u[2 * N + c] = uc[2];
+    T[c] = Tc; pr[c] = r * Tc;
+  }
+}
+
+/* Lattice sums of mass, momentum and total energy (rho E = (sum f|xi|^2 + sum g)/2)
+ * over fluid cells, for conservation checks. */
+void o39_conserved(const o39_params *p, const uint8_t *mask, const double *f,
+                   const double *g, double *out5) {
+  build_lattice();
+  int64_t N = (int64_t)p->nx * p->ny * p->nz;
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int64_t c = 0; c < N; ++c) {
+    if (mask[c] != M_FLUID) continue;
+    for (int i = 0; i < Q; ++i) {
+      double fi = f[c * Q + i];
+      double c2 = VEL[i][0] * VEL[i][0] + VEL[i][1] * VEL[i][1] + VEL[i][2] * VEL[i][2];
+      s[0] += fi;
+      s[1] += fi * VEL[i][0]; s[2] += fi * VEL[i][1]; s[3] += fi * VEL[i][2];
+      s[4] += 0.5 * (fi * c2 + g[c * Q + i]);
+    }
+  }
+  for (int k = 0; k < 5; ++k) out5[k] = s[k];
+}
