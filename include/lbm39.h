@@ -1,0 +1,183 @@
+/*
+ * lbm39.h -- C ABI of the GB300 (sm_103a) 13-moment guided-equilibrium
+ * double-distribution-function lattice Boltzmann step on D3Q39.
+ *
+ * Method: Latt, Coreixas, Beny, Parmigiani, "Efficient supersonic flows
+ * through high-order guided equilibrium with lattice Boltzmann",
+ * arXiv:1910.13515.  Sec. 2 defines the equilibrium (Eq. discrete-equilibrium,
+ * Eq. 13constraints, Eq. discrete-equilibrium-poly); Sec. 3 the lattice, the
+ * Newton-Raphson solve, BGK collide-and-stream and the Knudsen-number
+ * dependent relaxation time (Eq. DeltaAvg, Eq. alpha); Sec. 4 the boundary
+ * conditions (freestream equilibrium, first-order outflow, half-way
+ * bounce-back); Sec. 5 the per-cell equilibrium step table.
+ *
+ * Conventions shared by every call
+ * - A lattice has nx*ny*nz cells, x fastest: cell = x + nx*(y + ny*z).
+ * - Scalar fields are arrays of N = nx*ny*nz float64; velocity fields are 3
+ *   consecutive planes of N (u_x, then u_y, then u_z).
+ * - Temperatures are lattice temperatures: p = rho*T, c_s = sqrt(gamma*T).
+ * - Mask (uint8, N cells, device memory): 0 fluid, 1 solid (half-way
+ *   bounce-back), 2 freestream (far-field equilibrium), 3 outflow (copies the
+ *   post-collision populations of the cell whose x is clamped into
+ *   [3, nx-4]: zero gradient along x).  Codes 2 and 3 may appear only in the
+ *   3 outermost layers of a non-periodic axis (3 is the longest lattice
+ *   shift), code 3 only along x; those layers may hold no fluid cell; the
+ *   cell an outflow cell copies must be fluid or freestream.  A lattice with
+ *   no mask (NULL) is all fluid and fully periodic.
+ * - Ownership: the caller allocates and frees every device buffer (the
+ *   population and auxiliary buffers sized by lbm39_query_bytes, the mask,
+ *   the field arrays) and owns the CUDA stream.  The library keeps only a
+ *   small host handle.  There is no CPU fallback: every computation runs in
+ *   this library's CUDA kernels, and a call on a machine without a usable
+ *   GPU returns LBM39_ERR_CUDA.
+ * - Errors: every int-returning call returns LBM39_OK (0) or a negative
+ *   lbm39_status; nothing is thrown across the ABI.  lbm39_strerror names
+ *   the code.  Calls on one lattice are not thread-safe.
+ * - Asynchrony: lbm39_init, lbm39_step and lbm39_read enqueue work on the
+ *   lattice's stream and return; lbm39_sync, lbm39_stats and the *_host
+ *   calls wait for it.
+ */
+#ifndef LBM39_H
+#define LBM39_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM39_Q 39  /* discrete velocities of D3Q39 (Sec. 3) */
+#define LBM39_NM 13 /* moment constraints / Lagrange multipliers (Eq. 13constraints) */
+
+typedef enum {
+  LBM39_OK = 0,
+  LBM39_ERR_ARG = -1,     /* NULL pointer, bad size or parameter out of range */
+  LBM39_ERR_CUDA = -2,    /* a CUDA runtime call failed (no GPU, bad pointer, ...) */
+  LBM39_ERR_NEWTON = -3,  /* some cells failed the Newton solve (counted, see below) */
+  LBM39_ERR_TIMEOUT = -4, /* lbm39_sync gave up waiting */
+  LBM39_ERR_LATTICE = -5, /* velocity/weight tables differ from the compiled D3Q39 */
+  LBM39_ERR_MASK = -6,    /* mask violates the boundary-layer rules above */
+  LBM39_ERR_STATE = -7    /* call out of order (e.g. step before init) */
+} lbm39_status;
+
+typedef enum {
+  LBM39_FP64 = 0, /* populations, moments, Newton and collision in FP64 */
+  LBM39_MIXED = 1 /* populations stored in FP32 as deviations from a reference
+                     state, collision in FP32; moments and the constraint solve
+                     in FP64 (see lbm39_params.ref_rho / ref_T) */
+} lbm39_precision;
+
+/* Run parameters (Sec. 3).  lbm39_default_params fills the defaults. */
+typedef struct {
+  int32_t nx, ny, nz;       /* lattice size, each >= 1 */
+  int32_t periodic[3];      /* 1 = periodic axis; 0 = 3 boundary layers per end */
+  double gamma;             /* heat-capacity ratio, C_v = 1/(gamma-1) (Sec. 2); > 1 */
+  double tau;               /* BGK relaxation time tau_f = tau_g (Pr = 1); >= 0.5 */
+  int32_t kn_sensor;        /* 1: tau(eps) = tau*alpha(eps) (Eq. alpha); 0: plain BGK */
+  double newton_tol;        /* stop when max_k |G_k|/rho < tol (Sec. 5); default 1e-12 */
+  int32_t newton_maxit;     /* updates per solve before a cell counts as failed; 30 */
+  int32_t newton_min_upd;   /* updates taken even from a converged warm start; 1 */
+  int32_t init_maxit;       /* cold-start updates allowed in lbm39_init; 200 */
+  int32_t precision;        /* lbm39_precision */
+  double ref_rho, ref_T;    /* LBM39_MIXED reference state (rho_bar, T_bar) */
+  double rho_inf, u_inf[3], T_inf; /* far-field state held by freestream cells */
+} lbm39_params;
+
+typedef struct lbm39_lattice lbm39_lattice;
+
+/* Counters since lbm39_init, and the current conserved sums. */
+typedef struct {
+  int64_t time;             /* time steps taken since lbm39_init */
+  int64_t fluid_cells;
+  int64_t failed_cells;     /* Newton failures summed over cells and steps */
+  int64_t newton_updates;   /* Newton updates summed over cells and steps */
+  int64_t newton_hist[32];  /* cell-steps by number of updates (31 = 31 or more) */
+  int64_t eps_hist[4];      /* cell-steps by alpha branch of Eq. alpha */
+  double conserved[5];      /* sums over fluid cells of rho, rho u_x, rho u_y,
+                               rho u_z, rho E = (sum f|xi|^2 + sum g)/2 */
+} lbm39_stats_t;
+
+/* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice
+ * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 1,
+ * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5)). */
+void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
+
+/* The compiled D3Q39 velocity set (Sec. 3: (0,0,0), (1,0,0)_FS, (+-1,+-1,+-1),
+ * (2,0,0)_FS, (2,2,0)_FS, (3,0,0)_FS) in the library's population order,
+ * vel[3*i + d] (host, 39*3 int32), and Shan's E^39_{3,7} weights w[i] (host,
+ * 39 float64; lattice metadata only -- the method is quadrature-free, Sec. 2).
+ * Either pointer may be NULL.  Population i of a lattice moves by vel[i]. */
+int lbm39_velocities(int32_t* vel, double* w);
+
+/* Sizes in bytes of the two device buffers a lattice needs: the populations
+ * (39 f and 39 g planes, FP64 or FP32) and the auxiliary buffer (multipliers
+ * carried between steps for the warm start, counters, reduction scratch and
+ * host staging).  Both buffers must be 256-byte aligned. */
+int lbm39_query_bytes(const lbm39_params* p, size_t* pop_bytes, size_t* aux_bytes);
+
+/* Creates a lattice over caller-owned device buffers.  vel/w (host) must equal
+ * lbm39_velocities' tables (LBM39_ERR_LATTICE otherwise; w may be NULL).
+ * mask_dev: device mask of N cells or NULL (all fluid; needs every axis
+ * periodic).  The mask is validated (LBM39_ERR_MASK) and must stay unchanged
+ * and alive while the lattice exists.  cuda_stream: a cudaStream_t or NULL
+ * for the legacy default stream.  *out receives the handle. */
+int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, void* pop_buf,
+                 void* aux_buf, const uint8_t* mask_dev, void* cuda_stream,
+                 lbm39_lattice** out);
+
+/* Initial condition (Sec. 3): every fluid cell at its 13-moment equilibrium
+ * f = f^eq(rho, u, T), g = (2C_v - D) T f^eq, from a damped cold-start Newton
+ * (at most init_maxit updates).  rho, T: N float64; u: 3*N float64; all device
+ * pointers.  Resets time and counters.  Cells whose solve fails are counted
+ * (see lbm39_sync). */
+int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const double* T);
+
+/* As lbm39_init with host arrays: copies them to the device (staging inside
+ * the auxiliary buffer) on the lattice's stream and waits for the copies. */
+int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const double* T);
+
+/* Enqueues nsteps >= 0 time steps (Sec. 3: per fluid cell, macroscopic
+ * moments -> Maxwell-Boltzmann targets -> Newton from the previous step's
+ * multipliers -> f^eq, g^eq -> eps, alpha -> BGK on f and g -> streaming by
+ * shifts of up to 3 cells with the mask rules).  In-place (AA pattern):
+ * even and odd steps use two kernels over one population buffer. */
+int lbm39_step(lbm39_lattice* L, int64_t nsteps);
+
+/* Waits for the lattice's stream for at most timeout_us microseconds (< 0:
+ * no limit).  *failed_cells (may be NULL) receives the Newton failures
+ * since lbm39_init.  Returns LBM39_ERR_TIMEOUT if the work is still running,
+ * LBM39_ERR_NEWTON if failed_cells > 0, else LBM39_OK. */
+int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells);
+
+/* Enqueues the macroscopic fields of the current (pre-collision) state:
+ * rho, u (3 planes), T and p = rho*T, N float64 each, device pointers; any
+ * may be NULL.  Non-fluid cells read 0. */
+int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p);
+
+/* As lbm39_read into host arrays (staged through the auxiliary buffer);
+ * returns when the copies are done. */
+int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double* p);
+
+/* Waits for the stream and fills *s (counters and conserved sums). */
+int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s);
+
+/* Bytes of a checkpoint (populations, multipliers, time and parity). */
+size_t lbm39_checkpoint_bytes(const lbm39_lattice* L);
+
+/* Copies the full state into / from a caller buffer of
+ * lbm39_checkpoint_bytes bytes (host or device pointer).  A lattice loaded
+ * from a checkpoint continues bit-identically to the one that saved it. */
+int lbm39_save(lbm39_lattice* L, void* buf);
+int lbm39_load(lbm39_lattice* L, const void* buf);
+
+/* Releases the handle (not the caller's buffers).  NULL is a no-op. */
+void lbm39_destroy(lbm39_lattice* L);
+
+/* Static string naming a status code. */
+const char* lbm39_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM39_H */

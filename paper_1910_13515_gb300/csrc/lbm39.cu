@@ -1,0 +1,458 @@
+// lbm39.cu -- host runtime of the C ABI declared in include/lbm39.h.
+//
+// The library owns no device memory: every buffer is the caller's.  Each call
+// validates its arguments, enqueues kernels on the lattice's stream and maps
+// CUDA errors to LBM39_ERR_CUDA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/lbm39.h"
+#include "kernels.cuh"
+
+using namespace lbm39;
+
+namespace {
+
+constexpr int BLK = 64;                          // threads per block of the cell kernels
+constexpr size_t WS_BYTES = (size_t)BLK * WS_DOUBLES * sizeof(double);
+constexpr int RED_BLOCKS = 1024;                 // blocks of the conserved-sum reduction
+constexpr long long STAGE_CELLS = 1LL << 20;     // host staging chunk (cells)
+constexpr uint64_t CKPT_MAGIC = 0x3933424d4c424c31ull;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct AuxLayout {
+  size_t lam, ctr, heq, partials, result, stage, total;
+};
+
+long long plane_stride(long long N) { return (N + 31) / 32 * 32; }
+
+AuxLayout aux_layout(long long N) {
+  const long long Np = plane_stride(N);
+  AuxLayout a;
+  size_t off = 0;
+  a.lam = off; off = align256(off + sizeof(double) * NM * Np);
+  a.ctr = off; off = align256(off + sizeof(unsigned long long) * 64);
+  a.heq = off; off = align256(off + sizeof(double) * 2 * Q);
+  a.partials = off; off = align256(off + sizeof(double) * 5 * RED_BLOCKS);
+  a.result = off; off = align256(off + sizeof(double) * 8);
+  a.stage = off; off = align256(off + sizeof(double) * 6 * std::min(N, STAGE_CELLS));
+  a.total = off;
+  return a;
+}
+
+bool params_ok(const lbm39_params* p) {
+  if (!p) return false;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > (1LL << 31) - 1) return false;
+  if (!(p->gamma > 1.0) || !(p->tau >= 0.5) || !(p->newton_tol > 0.0)) return false;
+  if (p->newton_maxit < 1 || p->newton_maxit > 1000 || p->newton_min_upd < 0 ||
+      p->init_maxit < 1 || p->init_maxit > 10000)
+    return false;
+  if (p->precision != LBM39_FP64) return false;
+  for (int a = 0; a < 3; ++a) {
+    const int n = a == 0 ? p->nx : a == 1 ? p->ny : p->nz;
+    if (!p->periodic[a] && n < 7) return false;  // 3 boundary layers per end + fluid
+  }
+  return true;
+}
+
+}  // namespace
+
+struct lbm39_lattice {
+  lbm39_params p;
+  long long N = 0, Np = 0, fluid = 0;
+  void* pop = nullptr;
+  char* aux = nullptr;
+  AuxLayout lay{};
+  const uint8_t* mask = nullptr;
+  bool ghosts = false;
+  cudaStream_t stream = nullptr;
+  long long t = 0;
+  bool initialized = false;
+  Desc desc{};
+  unsigned long long* ctr() { return reinterpret_cast<unsigned long long*>(aux + lay.ctr); }
+  double* stage() { return reinterpret_cast<double*>(aux + lay.stage); }
+};
+
+#define CUDA_OK(x)                                   \
+  do {                                               \
+    if ((x) != cudaSuccess) return LBM39_ERR_CUDA;   \
+  } while (0)
+
+static int last_launch() { return cudaGetLastError() == cudaSuccess ? LBM39_OK : LBM39_ERR_CUDA; }
+
+static int set_smem_attrs() {
+  static bool done = false;
+  if (done) return LBM39_OK;
+  const int bytes = (int)WS_BYTES;
+  CUDA_OK(cudaFuncSetAttribute(k_step<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_step<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_init<BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_state_equilibrium<BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_macros<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_macros<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_conserved<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  CUDA_OK(cudaFuncSetAttribute(k_conserved<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+  return LBM39_OK;
+}
+
+extern "C" {
+
+void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx; p->ny = ny; p->nz = nz;
+  p->periodic[0] = p->periodic[1] = p->periodic[2] = 1;
+  p->gamma = 1.4;
+  p->tau = 0.6;
+  p->kn_sensor = 1;
+  p->newton_tol = 1e-12;
+  p->newton_maxit = 30;
+  p->newton_min_upd = 1;
+  p->init_maxit = 200;
+  p->precision = LBM39_FP64;
+  p->ref_rho = 1.0; p->ref_T = 0.5;
+  p->rho_inf = 1.0; p->T_inf = 0.5;
+}
+
+int lbm39_velocities(int32_t* vel, double* w) {
+  for (int i = 0; i < Q; ++i) {
+    if (vel) { vel[3 * i] = CX[i]; vel[3 * i + 1] = CY[i]; vel[3 * i + 2] = CZ[i]; }
+    if (w) w[i] = weight(i);
+  }
+  return LBM39_OK;
+}
+
+int lbm39_query_bytes(const lbm39_params* p, size_t* pop_bytes, size_t* aux_bytes) {
+  if (!params_ok(p)) return LBM39_ERR_ARG;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (pop_bytes) *pop_bytes = sizeof(double) * 2 * Q * plane_stride(N);
+  if (aux_bytes) *aux_bytes = aux_layout(N).total;
+  return LBM39_OK;
+}
+
+int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, void* pop_buf,
+                 void* aux_buf, const uint8_t* mask_dev, void* cuda_stream,
+                 lbm39_lattice** out) {
+  if (!out) return LBM39_ERR_ARG;
+  *out = nullptr;
+  if (!params_ok(p) || !vel || !pop_buf || !aux_buf) return LBM39_ERR_ARG;
+  if (((uintptr_t)pop_buf & 255) || ((uintptr_t)aux_buf & 255)) return LBM39_ERR_ARG;
+  for (int i = 0; i < Q; ++i) {
+    if (vel[3 * i] != CX[i] || vel[3 * i + 1] != CY[i] || vel[3 * i + 2] != CZ[i])
+      return LBM39_ERR_LATTICE;
+    if (w && w[i] != weight(i)) return LBM39_ERR_LATTICE;
+  }
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const bool all_periodic = p->periodic[0] && p->periodic[1] && p->periodic[2];
+  if (!mask_dev && !all_periodic) return LBM39_ERR_MASK;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  long long fluid = N;
+  bool ghosts = false;
+  if (mask_dev) {
+    std::vector<uint8_t> m(N);
+    CUDA_OK(cudaMemcpyAsync(m.data(), mask_dev, N, cudaMemcpyDeviceToHost, stream));
+    CUDA_OK(cudaStreamSynchronize(stream));
+    fluid = 0;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (long long c = 0; c < N; ++c) {
+      const int x = int(c % p->nx), y = int((c / p->nx) % p->ny), z = int(c / ((long long)p->nx * p->ny));
+      const int q[3] = {x, y, z};
+      bool layer = false;
+      for (int a = 0; a < 3; ++a)
+        if (!p->periodic[a] && (q[a] < 3 || q[a] >= n[a] - 3)) layer = true;
+      const uint8_t v = m[c];
+      if (v > 3) return LBM39_ERR_MASK;
+      if (v == MASK_FLUID) {
+        if (layer) return LBM39_ERR_MASK;
+        ++fluid;
+      }
+      if (v == MASK_FREE || v == MASK_OUT) {
+        if (!layer) return LBM39_ERR_MASK;
+        ghosts = true;
+      }
+      if (v == MASK_OUT) {
+        if (p->periodic[0] || !(x < 3 || x >= p->nx - 3)) return LBM39_ERR_MASK;
+        const int xc = std::min(std::max(x, 3), p->nx - 4);
+        const uint8_t t = m[c + (xc - x)];
+        if (t != MASK_FLUID && t != MASK_FREE) return LBM39_ERR_MASK;
+      }
+    }
+  }
+  if (set_smem_attrs() != LBM39_OK) return LBM39_ERR_CUDA;
+  lbm39_lattice* L = new (std::nothrow) lbm39_lattice;
+  if (!L) return LBM39_ERR_ARG;
+  L->p = *p;
+  L->N = N;
+  L->Np = plane_stride(N);
+  L->fluid = fluid;
+  L->pop = pop_buf;
+  L->aux = static_cast<char*>(aux_buf);
+  L->lay = aux_layout(N);
+  L->mask = mask_dev;
+  L->ghosts = ghosts;
+  L->stream = stream;
+  Desc& d = L->desc;
+  d.pop = static_cast<double*>(pop_buf);
+  d.lam = reinterpret_cast<double*>(L->aux + L->lay.lam);
+  d.mask = mask_dev;
+  d.ctr = L->ctr();
+  d.heq_inf = reinterpret_cast<const double*>(L->aux + L->lay.heq);
+  d.N = N;
+  d.Np = L->Np;
+  d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+  for (int a = 0; a < 3; ++a) d.per[a] = p->periodic[a] ? 1 : 0;
+  const double cv = 1.0 / (p->gamma - 1.0);
+  d.ph.tau = p->tau;
+  d.ph.cg = 2.0 * cv - D;
+  d.ph.inv_2cv = 1.0 / (2.0 * cv);
+  d.ph.tol = p->newton_tol;
+  d.ph.maxit = p->newton_maxit;
+  d.ph.min_upd = p->newton_min_upd;
+  d.ph.kn_sensor = p->kn_sensor ? 1 : 0;
+  // far-field equilibrium for freestream cells (counts failures in ctr[CTR_N])
+  unsigned long long* fail_slot = L->ctr() + CTR_N;
+  if (cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, stream) != cudaSuccess) {
+    delete L;
+    return LBM39_ERR_CUDA;
+  }
+  k_state_equilibrium<BLK><<<1, BLK, WS_BYTES, stream>>>(
+      d.ph, p->rho_inf, p->u_inf[0], p->u_inf[1], p->u_inf[2], p->T_inf,
+      reinterpret_cast<double*>(L->aux + L->lay.heq), p->init_maxit, fail_slot);
+  unsigned long long nfail = 0;
+  if (last_launch() != LBM39_OK ||
+      cudaMemcpyAsync(&nfail, fail_slot, sizeof nfail, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    delete L;
+    return LBM39_ERR_CUDA;
+  }
+  if (ghosts && nfail) {
+    delete L;
+    return LBM39_ERR_NEWTON;
+  }
+  *out = L;
+  return LBM39_OK;
+}
+
+static int init_range(lbm39_lattice* L, const double* rho, const double* u, long long us,
+                      const double* T, long long c0, long long len) {
+  const unsigned grid = (unsigned)((len + BLK - 1) / BLK);
+  k_init<BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, c0, len,
+                                                  L->p.init_maxit);
+  return last_launch();
+}
+
+static int init_begin(lbm39_lattice* L) {
+  CUDA_OK(cudaMemsetAsync(L->pop, 0, sizeof(double) * 2 * Q * L->Np, L->stream));
+  CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));
+  L->t = 0;
+  L->initialized = true;
+  return LBM39_OK;
+}
+
+int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
+  if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
+  int rc = init_begin(L);
+  if (rc) return rc;
+  return init_range(L, rho, u, L->N, T, 0, L->N);
+}
+
+int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
+  if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
+  int rc = init_begin(L);
+  if (rc) return rc;
+  const long long C = std::min(L->N, STAGE_CELLS);
+  double* s = L->stage();
+  for (long long c0 = 0; c0 < L->N; c0 += C) {
+    const long long n = std::min(C, L->N - c0);
+    CUDA_OK(cudaMemcpyAsync(s, rho + c0, sizeof(double) * n, cudaMemcpyHostToDevice, L->stream));
+    for (int a = 0; a < 3; ++a)
+      CUDA_OK(cudaMemcpyAsync(s + (1 + a) * C, u + a * L->N + c0, sizeof(double) * n,
+                              cudaMemcpyHostToDevice, L->stream));
+    CUDA_OK(cudaMemcpyAsync(s + 4 * C, T + c0, sizeof(double) * n, cudaMemcpyHostToDevice, L->stream));
+    rc = init_range(L, s, s + C, C, s + 4 * C, c0, n);
+    if (rc) return rc;
+  }
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  return LBM39_OK;
+}
+
+int lbm39_step(lbm39_lattice* L, int64_t nsteps) {
+  if (!L || nsteps < 0) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  const unsigned grid = (unsigned)((L->N + BLK - 1) / BLK);
+  const unsigned fgrid = (unsigned)((L->N + 255) / 256);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if ((L->t & 1) == 0) {
+      k_step<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (L->ghosts) k_fill_even<<<fgrid, 256, 0, L->stream>>>(L->desc);
+    } else {
+      k_step<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (L->ghosts) k_fill_odd<<<fgrid, 256, 0, L->stream>>>(L->desc);
+    }
+    if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
+    ++L->t;
+  }
+  return LBM39_OK;
+}
+
+int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells) {
+  if (!L) return LBM39_ERR_ARG;
+  cudaEvent_t ev;
+  CUDA_OK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (cudaEventRecord(ev, L->stream) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return LBM39_ERR_CUDA;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaError_t q;
+  while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+    if (timeout_us >= 0 &&
+        std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0)
+                .count() > timeout_us) {
+      cudaEventDestroy(ev);
+      return LBM39_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  if (q != cudaSuccess) return LBM39_ERR_CUDA;
+  unsigned long long nf = 0;
+  CUDA_OK(cudaMemcpyAsync(&nf, L->ctr() + CTR_FAILED, sizeof nf, cudaMemcpyDeviceToHost, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  if (failed_cells) *failed_cells = (int64_t)nf;
+  return nf ? LBM39_ERR_NEWTON : LBM39_OK;
+}
+
+static int read_range(lbm39_lattice* L, double* rho, double* u, long long us, double* T,
+                      double* p, long long c0, long long len) {
+  const unsigned grid = (unsigned)((len + BLK - 1) / BLK);
+  if (L->t & 1)
+    k_macros<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
+  else
+    k_macros<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
+  return last_launch();
+}
+
+int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
+  if (!L) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  return read_range(L, rho, u, L->N, T, p, 0, L->N);
+}
+
+int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
+  if (!L) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  const long long C = std::min(L->N, STAGE_CELLS);
+  double* s = L->stage();
+  for (long long c0 = 0; c0 < L->N; c0 += C) {
+    const long long n = std::min(C, L->N - c0);
+    int rc = read_range(L, rho ? s : nullptr, u ? s + C : nullptr, C, T ? s + 4 * C : nullptr,
+                        p ? s + 5 * C : nullptr, c0, n);
+    if (rc) return rc;
+    if (rho) CUDA_OK(cudaMemcpyAsync(rho + c0, s, sizeof(double) * n, cudaMemcpyDeviceToHost, L->stream));
+    if (u)
+      for (int a = 0; a < 3; ++a)
+        CUDA_OK(cudaMemcpyAsync(u + a * L->N + c0, s + (1 + a) * C, sizeof(double) * n,
+                                cudaMemcpyDeviceToHost, L->stream));
+    if (T) CUDA_OK(cudaMemcpyAsync(T + c0, s + 4 * C, sizeof(double) * n, cudaMemcpyDeviceToHost, L->stream));
+    if (p) CUDA_OK(cudaMemcpyAsync(p + c0, s + 5 * C, sizeof(double) * n, cudaMemcpyDeviceToHost, L->stream));
+    CUDA_OK(cudaStreamSynchronize(L->stream));
+  }
+  return LBM39_OK;
+}
+
+int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
+  if (!L || !s) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  double* partials = reinterpret_cast<double*>(L->aux + L->lay.partials);
+  double* result = reinterpret_cast<double*>(L->aux + L->lay.result);
+  const unsigned grid = (unsigned)std::min<long long>(RED_BLOCKS, (L->N + BLK - 1) / BLK);
+  if (L->t & 1)
+    k_conserved<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, partials);
+  else
+    k_conserved<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, partials);
+  k_sum_partials<<<1, 32, 0, L->stream>>>(partials, (int)grid, result);
+  if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
+  unsigned long long c[CTR_N];
+  double r5[5];
+  CUDA_OK(cudaMemcpyAsync(c, L->ctr(), sizeof c, cudaMemcpyDeviceToHost, L->stream));
+  CUDA_OK(cudaMemcpyAsync(r5, result, sizeof r5, cudaMemcpyDeviceToHost, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  std::memset(s, 0, sizeof(*s));
+  s->time = L->t;
+  s->fluid_cells = L->fluid;
+  s->failed_cells = (int64_t)c[CTR_FAILED];
+  s->newton_updates = (int64_t)c[CTR_UPDATES];
+  for (int k = 0; k < 32; ++k) s->newton_hist[k] = (int64_t)c[CTR_HIST + k];
+  for (int k = 0; k < 4; ++k) s->eps_hist[k] = (int64_t)c[CTR_EPS + k];
+  for (int k = 0; k < 5; ++k) s->conserved[k] = r5[k];
+  return LBM39_OK;
+}
+
+size_t lbm39_checkpoint_bytes(const lbm39_lattice* L) {
+  if (!L) return 0;
+  return 256 + sizeof(double) * 2 * Q * L->Np + sizeof(double) * NM * L->Np;
+}
+
+int lbm39_save(lbm39_lattice* L, void* buf) {
+  if (!L || !buf) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  uint64_t hdr[32] = {0};
+  hdr[0] = CKPT_MAGIC;
+  hdr[1] = (uint64_t)L->t;
+  hdr[2] = (uint64_t)L->N;
+  hdr[3] = (uint64_t)L->p.precision;
+  char* b = static_cast<char*>(buf);
+  const size_t pb = sizeof(double) * 2 * Q * L->Np, lb = sizeof(double) * NM * L->Np;
+  CUDA_OK(cudaMemcpyAsync(b, hdr, sizeof hdr, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaMemcpyAsync(b + 256, L->pop, pb, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaMemcpyAsync(b + 256 + pb, L->desc.lam, lb, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  return LBM39_OK;
+}
+
+int lbm39_load(lbm39_lattice* L, const void* buf) {
+  if (!L || !buf) return LBM39_ERR_ARG;
+  uint64_t hdr[32];
+  const char* b = static_cast<const char*>(buf);
+  CUDA_OK(cudaMemcpyAsync(hdr, b, sizeof hdr, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  if (hdr[0] != CKPT_MAGIC || hdr[2] != (uint64_t)L->N || hdr[3] != (uint64_t)L->p.precision)
+    return LBM39_ERR_ARG;
+  const size_t pb = sizeof(double) * 2 * Q * L->Np, lb = sizeof(double) * NM * L->Np;
+  CUDA_OK(cudaMemcpyAsync(L->pop, b + 256, pb, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaMemcpyAsync(L->desc.lam, b + 256 + pb, lb, cudaMemcpyDefault, L->stream));
+  CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  L->t = (long long)hdr[1];
+  L->initialized = true;
+  return LBM39_OK;
+}
+
+void lbm39_destroy(lbm39_lattice* L) { delete L; }
+
+const char* lbm39_strerror(int status) {
+  switch (status) {
+    case LBM39_OK: return "ok";
+    case LBM39_ERR_ARG: return "invalid argument";
+    case LBM39_ERR_CUDA: return "CUDA runtime error";
+    case LBM39_ERR_NEWTON: return "Newton solve failed in some cells";
+    case LBM39_ERR_TIMEOUT: return "timed out waiting for the GPU";
+    case LBM39_ERR_LATTICE: return "velocity or weight table differs from the compiled D3Q39";
+    case LBM39_ERR_MASK: return "mask violates the boundary-layer rules";
+    case LBM39_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

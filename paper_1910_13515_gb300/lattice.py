@@ -1,0 +1,156 @@
+"""Lattice: one D3Q39 DDF lattice on one GPU, over torch-allocated device buffers.
+
+PyTorch provides the device memory and the stream; every computation is a
+kernel of liblbm39 called through the C ABI (``lbm39`` module).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import lbm39 as C
+from .inputs import Setup
+
+
+def velocities():
+    """(vel (39,3) int32, w (39,) float64) in the library's population order."""
+    vel = np.zeros((C.Q, 3), np.int32)
+    w = np.zeros(C.Q)
+    C.check(C.lbm39_velocities(vel.ctypes.data, w.ctypes.data), "lbm39_velocities")
+    return vel, w
+
+
+def params_from_setup(s: Setup, precision: int = C.LBM39_FP64, **over) -> C.lbm39_params:
+    p = C.lbm39_default_params(s.nx, s.ny, s.nz)
+    for a in range(3):
+        p.periodic[a] = int(s.periodic[a])
+        p.u_inf[a] = float(s.u_inf[a])
+    p.gamma = s.gamma
+    p.tau = s.tau
+    p.kn_sensor = int(s.kn_sensor)
+    p.rho_inf = s.rho_inf
+    p.T_inf = s.T_inf
+    p.precision = precision
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+class Lattice:
+    """Owns the device buffers of one lattice and its library handle."""
+
+    def __init__(self, params: C.lbm39_params, mask: np.ndarray | None = None,
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None):
+        self.params = params
+        self.device = torch.device(device)
+        self.N = params.nx * params.ny * params.nz
+        rc, pop_b, aux_b = C.lbm39_query_bytes(params)
+        C.check(rc, "lbm39_query_bytes")
+        # 256-byte aligned by the caching allocator; float64 storage keeps 8-byte units
+        self.pop = torch.empty((pop_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.aux = torch.empty((aux_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.mask = None
+        self.has_ghosts = mask is not None and bool(
+            np.isin(np.asarray(mask), (2, 3)).any())
+        if mask is not None:
+            self.mask = torch.as_tensor(np.ascontiguousarray(mask, np.uint8).reshape(-1),
+                                        device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        vel, w = velocities()
+        self._vel, self._w = vel, w
+        rc, h = C.lbm39_create(params, vel.ctypes.data, w.ctypes.data, self.pop.data_ptr(),
+                               self.aux.data_ptr(),
+                               self.mask.data_ptr() if self.mask is not None else None,
+                               self.stream.cuda_stream)
+        C.check(rc, "lbm39_create")
+        self.h = h
+
+    @classmethod
+    def from_setup(cls, s: Setup, precision: int = C.LBM39_FP64, device="cuda", stream=None,
+                   **over) -> "Lattice":
+        L = cls(params_from_setup(s, precision, **over), s.mask, device, stream)
+        L.init(s.rho, s.u, s.T)
+        return L
+
+    def close(self):
+        if getattr(self, "h", None):
+            C.lbm39_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state -----------------------------------------------------------------------------
+    def _dev(self, a, n):
+        t = torch.as_tensor(np.ascontiguousarray(a, np.float64).reshape(-1), device=self.device) \
+            if not isinstance(a, torch.Tensor) else a.to(self.device, torch.float64).contiguous()
+        assert t.numel() == n
+        return t
+
+    def init(self, rho, u, T):
+        r, uu, t = self._dev(rho, self.N), self._dev(u, 3 * self.N), self._dev(T, self.N)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        C.check(C.lbm39_init(self.h, r.data_ptr(), uu.data_ptr(), t.data_ptr()), "lbm39_init")
+        self._keep = (r, uu, t)  # alive until the kernels have read them
+        self.sync()
+
+    def init_host(self, rho, u, T):
+        """Initial condition from host arrays (copied through the library's staging)."""
+        r = np.ascontiguousarray(rho, np.float64)
+        uu = np.ascontiguousarray(u, np.float64)
+        t = np.ascontiguousarray(T, np.float64)
+        C.check(C.lbm39_init_host(self.h, r.ctypes.data, uu.ctypes.data, t.ctypes.data),
+                "lbm39_init_host")
+
+    def step(self, n: int = 1):
+        C.check(C.lbm39_step(self.h, int(n)), "lbm39_step")
+
+    def sync(self, timeout_us: int = -1) -> int:
+        rc, failed = C.lbm39_sync(self.h, timeout_us)
+        if rc not in (C.LBM39_OK, C.LBM39_ERR_NEWTON):
+            C.check(rc, "lbm39_sync")
+        return failed
+
+    def read(self):
+        """(rho, u (3,N), T, p) as float64 device tensors."""
+        out = torch.empty(6, self.N, dtype=torch.float64, device=self.device)
+        C.check(C.lbm39_read(self.h, out[0].data_ptr(), out[1].data_ptr(), out[4].data_ptr(),
+                             out[5].data_ptr()), "lbm39_read")
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out[0], out[1:4], out[4], out[5]
+
+    def read_numpy(self):
+        r, u, T, p = self.read()
+        self.stream.synchronize()
+        return r.cpu().numpy(), u.cpu().numpy(), T.cpu().numpy(), p.cpu().numpy()
+
+    def read_host(self, out: np.ndarray | None = None):
+        """Host read-out through the library's staging: (rho, u, T, p) numpy arrays."""
+        if out is None:
+            out = np.empty((6, self.N))
+        C.check(C.lbm39_read_host(self.h, out[0].ctypes.data, out[1].ctypes.data,
+                                  out[4].ctypes.data, out[5].ctypes.data), "lbm39_read_host")
+        return out[0], out[1:4], out[4], out[5]
+
+    def stats(self) -> C.lbm39_stats_t:
+        rc, s = C.lbm39_stats(self.h)
+        C.check(rc, "lbm39_stats")
+        return s
+
+    def checkpoint(self) -> torch.Tensor:
+        n = C.lbm39_checkpoint_bytes(self.h)
+        buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        C.check(C.lbm39_save(self.h, buf.data_ptr()), "lbm39_save")
+        return buf
+
+    def restore(self, buf: torch.Tensor):
+        C.check(C.lbm39_load(self.h, buf.data_ptr()), "lbm39_load")
+
+    @property
+    def time(self) -> int:
+        return int(self.stats().time)

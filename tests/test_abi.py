@@ -1,0 +1,97 @@
+"""Host-only checks of the C ABI: the library builds, loads and exports every symbol that
+include/lbm39.h declares; argument validation that happens before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1910_13515_gb300 import build
+    build.build()
+    from paper_1910_13515_gb300 import lbm39
+    return lbm39
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbm39.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm39_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(C):
+    names = declared_functions()
+    assert "lbm39_step" in names and "lbm39_create" in names and len(names) >= 16
+    lib = ctypes.CDLL(C.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_velocity_table_matches_the_paper_set_and_oracle(C, oracle):
+    vel = np.zeros((39, 3), np.int32)
+    w = np.zeros(39)
+    assert C.lbm39_velocities(vel.ctypes.data, w.ctypes.data) == 0
+    ov, ow, oopp = oracle.lattice()
+    lib_map = {tuple(v): wi for v, wi in zip(vel, w)}
+    orc_map = {tuple(v): wi for v, wi in zip(ov, ow)}
+    assert lib_map.keys() == orc_map.keys()
+    for k in lib_map:
+        assert lib_map[k] == orc_map[k]
+    # rest velocity first, then (xi, -xi) pairs
+    assert tuple(vel[0]) == (0, 0, 0)
+    for i in range(1, 39, 2):
+        assert np.array_equal(vel[i], -vel[i + 1])
+
+
+def test_default_params_and_sizes(C):
+    p = C.lbm39_default_params(10, 8, 6)
+    assert (p.nx, p.ny, p.nz) == (10, 8, 6) and list(p.periodic) == [1, 1, 1]
+    assert p.gamma == 1.4 and p.newton_tol == 1e-12 and p.newton_min_upd == 1
+    rc, pop_b, aux_b = C.lbm39_query_bytes(p)
+    assert rc == 0
+    N = 480
+    Np = (N + 31) // 32 * 32
+    assert pop_b == 78 * 8 * Np
+    assert aux_b >= 13 * 8 * Np
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("tau", 0.4),
+                                         ("newton_tol", 0.0), ("newton_maxit", 0),
+                                         ("precision", 7)])
+def test_bad_params_rejected(C, field, value):
+    p = C.lbm39_default_params(8, 8, 8)
+    setattr(p, field, value)
+    rc, _, _ = C.lbm39_query_bytes(p)
+    assert rc == C.LBM39_ERR_ARG
+
+
+def test_create_validation_before_any_gpu_call(C):
+    p = C.lbm39_default_params(8, 8, 8)
+    vel = np.zeros((39, 3), np.int32)
+    C.lbm39_velocities(vel.ctypes.data, None)
+    bad = vel.copy()
+    bad[[1, 2]] = bad[[2, 1]]
+    fake = 1 << 20  # never dereferenced: validation fails first
+    rc, h = C.lbm39_create(p, bad.ctypes.data, None, fake, fake, None, None)
+    assert rc == C.LBM39_ERR_LATTICE and not h
+    rc, h = C.lbm39_create(p, vel.ctypes.data, None, fake + 8, fake, None, None)
+    assert rc == C.LBM39_ERR_ARG  # misaligned buffer
+    p.periodic[0] = 0
+    rc, h = C.lbm39_create(p, vel.ctypes.data, None, fake, fake, None, None)
+    assert rc == C.LBM39_ERR_MASK  # non-periodic axis needs a mask
+
+
+def test_null_handles_and_strerror(C):
+    assert C.lbm39_step(None, 1) == C.LBM39_ERR_ARG
+    assert C.lbm39_sync(None, 0)[0] == C.LBM39_ERR_ARG
+    assert C.lbm39_read(None, None, None, None, None) == C.LBM39_ERR_ARG
+    assert C.lbm39_checkpoint_bytes(None) == 0
+    C.lbm39_destroy(None)
+    for code in range(-7, 1):
+        assert C.lbm39_strerror(code) != "unknown status"
+    assert C.lbm39_strerror(-99) == "unknown status"
