@@ -32,6 +32,8 @@ WORKLOADS = {
               "seed 0, tau=0.55, alpha(eps) on",
     "box384": "3-D periodic box 384^3, solenoidal velocity rms Ma=0.8, +-5% rho/T noise, "
               "seed 0, tau=0.55, alpha(eps) on",
+    "box128": "3-D periodic box 128^3 (profiling size), solenoidal velocity rms Ma=0.8, "
+              "+-5% rho/T noise, seed 0, tau=0.55, alpha(eps) on",
     "sod": "Sod tube 400x1x1, outflow ends, tau=0.5 with alpha(eps)",
 }
 
@@ -51,6 +53,8 @@ def make_setup(name: str):
         return inputs.box(n=256, seed=0)
     if name == "box384":
         return inputs.box(n=384, seed=0)
+    if name == "box128":
+        return inputs.box(n=128, seed=0)
     if name == "sod":
         return inputs.sod(400)
     raise ValueError(name)

@@ -77,7 +77,7 @@ typedef struct {
   int32_t kn_sensor;        /* 1: tau(eps) = tau*alpha(eps) (Eq. alpha); 0: plain BGK */
   double newton_tol;        /* stop when max_k |G_k|/rho < tol (Sec. 5); default 1e-12 */
   int32_t newton_maxit;     /* updates per solve before a cell counts as failed; 30 */
-  int32_t newton_min_upd;   /* updates taken even from a converged warm start; 1 */
+  int32_t newton_min_upd;   /* updates taken even from a converged warm start; 0 */
   int32_t init_maxit;       /* cold-start updates allowed in lbm39_init; 200 */
   int32_t precision;        /* lbm39_precision */
   double ref_rho, ref_T;    /* LBM39_MIXED reference state (rho_bar, T_bar) */
@@ -99,7 +99,7 @@ typedef struct {
 } lbm39_stats_t;
 
 /* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice
- * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 1,
+ * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 0,
  * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5)). */
 void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
 
@@ -170,6 +170,13 @@ size_t lbm39_checkpoint_bytes(const lbm39_lattice* L);
  * from a checkpoint continues bit-identically to the one that saved it. */
 int lbm39_save(lbm39_lattice* L, void* buf);
 int lbm39_load(lbm39_lattice* L, const void* buf);
+
+/* Diagnostic of the library's FP64 exponential (the table-driven method of
+ * Tang, ACM TOMS 15(2) 1989, used for every f^eq evaluation): for n device
+ * values x, writes y[i] = that exponential and ref[i] = CUDA's exp(x[i]), so a
+ * caller can bound its error.  x, y, ref: device pointers of n float64;
+ * cuda_stream as in lbm39_create.  Returns after enqueueing. */
+int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void* cuda_stream);
 
 /* Releases the handle (not the caller's buffers).  NULL is a no-op. */
 void lbm39_destroy(lbm39_lattice* L);

@@ -268,8 +268,9 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
  *          lam <- lam - J^{-1} G } until max|G| < tol.
  * reading (stopping and damping are not specified beyond "norm below 1e-12"):
- *  - at least `min_upd` updates are taken, so a converged warm start is still
- *    polished by one full step;
+ *  - at least `min_upd` updates are taken (default 0: a warm start whose
+ *    residual is already at round-off takes none, as the paper reports for
+ *    wide areas of its airfoil flow, Sec. 4);
  *  - a solve that lands between tol/100 and tol (above the round-off floor of
  *    the residual) takes one more full "polishing" step from there; with
  *    quadratic convergence that step ends at round-off, so the collision

@@ -171,7 +171,7 @@ def gaussian_guess(u, T) -> np.ndarray:
     return out
 
 
-def newton(m, lam0, tol=1e-12, maxit=30, min_upd=1):
+def newton(m, lam0, tol=1e-12, maxit=30, min_upd=0):
     """Returns (lam, F, n_updates, status)."""
     lam = _f64(lam0).copy()
     F = np.zeros(Q)
@@ -197,7 +197,7 @@ class Config:
     kn_sensor: int = 1
     newton_tol: float = 1e-12
     newton_maxit: int = 30
-    newton_min_upd: int = 1
+    newton_min_upd: int = 0
     rho_inf: float = 1.0
     u_inf: tuple = (0.0, 0.0, 0.0)
     T_inf: float = 0.5

@@ -1,30 +1,41 @@
-// cell.cuh -- per-cell arithmetic of the 13-moment DDF step (FP64).
+// cell.cuh -- per-cell arithmetic of the 13-moment DDF step.
 //
 // Every function runs in one thread for one cell.  Per-cell arrays that do
 // not fit in registers live in shared memory with a stride of the block size
 // (WS), so a warp touches 32 consecutive doubles and hits no bank conflict.
+//
+// The GB300 issues FP64 at about 1/64 of the FP32 rate, so the FP64 step is
+// bound by its FP64 operation count.  The sums over the 39 velocities come
+// from gen_d3q39.py (sign-orbit butterflies: the same sums, reorganised), the
+// exponential is exp_tang (9 FP64 operations), and the Knudsen sensor is
+// screened in FP32 and recomputed in FP64 only near a threshold of Eq. (alpha),
+// so alpha is the one an FP64 evaluation gives.
 #pragma once
 #include <cmath>
 
 #include "d3q39.cuh"
+#include "d3q39_gen.cuh"
+#include "expd.cuh"
 
 namespace lbm39 {
 
 // Strided per-thread view of a shared-memory array.
-template <int BLK>
-struct WS {
-  double* p;
-  __device__ __forceinline__ double& operator[](int k) const { return p[k * BLK]; }
-  __device__ __forceinline__ WS at(int k) const { return WS{p + k * BLK}; }
+template <class V, int BLK>
+struct WSV {
+  V* p;
+  __device__ __forceinline__ V& operator[](int k) const { return p[k * BLK]; }
+  __device__ __forceinline__ WSV at(int k) const { return WSV{p + k * BLK}; }
 };
+template <int BLK>
+using WS = WSV<double, BLK>;
 
 // Per-thread workspace layout (units of BLK doubles).
-constexpr int WS_F = 0;         // f populations (39)
-constexpr int WS_G = 39;        // g populations (39)
-constexpr int WS_E = 78;        // normalised equilibrium F_i (39)
-constexpr int WS_LAM = 117;     // multipliers (13)
-constexpr int WS_M = 130;       // normalised targets (13)
-constexpr int WS_DOUBLES = 143;
+constexpr int WS_E = 0;         // normalised equilibrium F_i (39)
+constexpr int WS_LAM = 39;      // multipliers (13)
+constexpr int WS_M = 52;        // normalised targets (13)
+constexpr int WS_LT = 65;       // trial multipliers of the Newton step (13)
+constexpr int WS_DL = 78;       // Newton direction (13)
+constexpr int WS_DOUBLES = 91;
 
 // Lattice-wide constants of one run.
 struct Phys {
@@ -51,34 +62,65 @@ __device__ __forceinline__ void targets(double ux, double uy, double uz, double 
   m[10] = ux * h; m[11] = uy * h; m[12] = uz * h;
 }
 
+// Float view of a double by integer operations (truncated to 23 mantissa bits):
+// relative error below 2^-23 for |x| in float's normal range, 0 below it.
+__device__ __forceinline__ float trunc_float(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e >= 255) return __double2float_rn(x);  // out of range, inf, NaN
+  const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)e << 23) |
+                        (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+  return e > 0 ? __uint_as_float(bits) : 0.0f;
+}
+
+// Exact float -> double by integer operations (normal floats and zero; other
+// values take the conversion instruction).
+__device__ __forceinline__ double exact_double(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xff;
+  if (e == 0 || e == 255) return (double)v;
+  const unsigned hi = (b & 0x80000000u) | ((e + (1023 - 127)) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// exp of the 39 exponents parked in F (stride BLK), by CUDA's exp: the rare
+// path for arguments outside exp_tang_core's range.
+template <int BLK>
+__device__ __noinline__ void exp_all_slow(double* Fp) {
+  for (int i = 0; i < Q; ++i) Fp[i * BLK] = exp(Fp[i * BLK]);
+}
+
 // F_i = exp(sum_k lam_k phi_k(xi_i)) (Eq. discrete-equilibrium / rho) into F,
 // and the constraint residual G_k = sum_i F_i phi_k(xi_i) - m_k (Eq. constraints).
 template <int BLK>
-__device__ __forceinline__ void eval_equilibrium(const double (&l)[NM], WS<BLK> F, WS<BLK> m,
+__device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> F, WS<BLK> m,
                                                  double (&G)[NM]) {
-  double s[NM];
+  double x[Q];
+  {
+    double l[NM];
 #pragma unroll
-  for (int k = 0; k < NM; ++k) s[k] = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    double e = l[0];
-    static_for<1, NM>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      constexpr int c = phi(k, i);
-      if constexpr (c == 1) e += l[k];
-      else if constexpr (c == -1) e -= l[k];
-      else if constexpr (c != 0) e = fma((double)c, l[k], e);
-    });
-    const double Fi = exp(e);
-    F[i] = Fi;
-    static_for<0, NM>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      constexpr int c = phi(k, i);
-      if constexpr (c == 1) s[k] += Fi;
-      else if constexpr (c == -1) s[k] -= Fi;
-      else if constexpr (c != 0) s[k] = fma((double)c, Fi, s[k]);
-    });
-  });
+    for (int k = 0; k < NM; ++k) l[k] = lam[k];
+    gen::exponents(l, x);
+  }
+  int wide = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
+  if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
+#pragma unroll
+    for (int i = 0; i < Q; ++i) F[i] = x[i];
+    exp_all_slow<BLK>(F.p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) x[i] = F[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      x[i] = exp_tang_core(x[i]);
+      F[i] = x[i];
+    }
+  }
+  double s[NM];
+  gen::moments_s<double>(x, s);
 #pragma unroll
   for (int k = 0; k < NM; ++k) G[k] = s[k] - m[k];
 }
@@ -100,78 +142,86 @@ __device__ __forceinline__ double sum_sq(const double (&v)[NM]) {
   return s;
 }
 
-// Jacobian J_kl = sum_i F_i phi_k phi_l (Sec. 5 step table), packed lower
-// triangle, then in place LDL^T and the solve J x = b (b overwritten by x).
-// Returns false if a pivot is not positive (J not numerically SPD).
-template <int BLK>
-__device__ __forceinline__ bool jacobian_solve(WS<BLK> F, double (&b)[NM]) {
-  double J[NTRI];
-#pragma unroll
-  for (int t = 0; t < NTRI; ++t) J[t] = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const double Fi = F[i];
-    static_for<0, NM>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      static_for<0, k + 1>([&](auto L) {
-        constexpr int l = decltype(L)::value;
-        constexpr int c = phi(k, i) * phi(l, i);
-        if constexpr (c == 1) J[tri(k, l)] += Fi;
-        else if constexpr (c == -1) J[tri(k, l)] -= Fi;
-        else if constexpr (c != 0) J[tri(k, l)] = fma((double)c, Fi, J[tri(k, l)]);
-      });
-    });
-  });
+// In-place LDL^T of a packed symmetric 13x13 J (unit-lower L below a diagonal
+// D) and the solve J x = b (b overwritten by x).  False if a pivot is not
+// positive (J not numerically SPD).
+template <class T>
+__device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
   bool ok = true;
-  // LDL^T: diagonal d_j on J[tri(j,j)], unit-lower L below it.
+  T rd[NM];
   static_for<0, NM>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
-    double v[NM];
+    T v[NM];
     static_for<0, j>([&](auto K) {
       constexpr int k = decltype(K)::value;
       v[k] = J[tri(j, k)] * J[tri(k, k)];
     });
-    double dj = J[tri(j, j)];
+    T dj = J[tri(j, j)];
     static_for<0, j>([&](auto K) {
       constexpr int k = decltype(K)::value;
       dj = fma(-J[tri(j, k)], v[k], dj);
     });
-    ok = ok && (dj > 0.0);
+    ok = ok && (dj > T(0));
     J[tri(j, j)] = dj;
-    const double rj = 1.0 / dj;
+    rd[j] = T(1) / dj;
     static_for<j + 1, NM>([&](auto II) {
       constexpr int i = decltype(II)::value;
-      double a = J[tri(i, j)];
+      T a = J[tri(i, j)];
       static_for<0, j>([&](auto K) {
         constexpr int k = decltype(K)::value;
         a = fma(-J[tri(i, k)], v[k], a);
       });
-      J[tri(i, j)] = a * rj;
+      J[tri(i, j)] = a * rd[j];
     });
   });
-  // L y = b
-  static_for<1, NM>([&](auto II) {
+  static_for<1, NM>([&](auto II) {  // L y = b
     constexpr int i = decltype(II)::value;
-    double a = b[i];
+    T a = b[i];
     static_for<0, i>([&](auto K) {
       constexpr int k = decltype(K)::value;
       a = fma(-J[tri(i, k)], b[k], a);
     });
     b[i] = a;
   });
-  // D z = y
 #pragma unroll
-  for (int i = 0; i < NM; ++i) b[i] = b[i] / J[tri(i, i)];
-  // L^T x = z
-  static_for<0, NM - 1>([&](auto II) {
+  for (int i = 0; i < NM; ++i) b[i] *= rd[i];  // D z = y
+  static_for<0, NM - 1>([&](auto II) {  // L^T x = z
     constexpr int i = NM - 2 - decltype(II)::value;
-    double a = b[i];
+    T a = b[i];
     static_for<i + 1, NM>([&](auto K) {
       constexpr int k = decltype(K)::value;
       a = fma(-J[tri(k, i)], b[k], a);
     });
     b[i] = a;
   });
+  return ok;
+}
+
+// Newton direction: J = sum_i F_i phi phi^T (Sec. 5 step table), J delta = b,
+// b and delta in dl.  FP64 path: J and LDL^T in FP64.  Precision form: in
+// FP32 (the residual and the update stay FP64, so the iteration still
+// converges to the FP64 root).
+template <int BLK, bool MIXED>
+__device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
+  if constexpr (!MIXED) {
+    double J[NTRI], s[NM], b[NM];
+    gen::moments<double>(F, s, J);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) b[k] = dl[k];
+    const bool ok = ldlt_solve<double>(J, b);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) dl[k] = b[k];
+    return ok;
+  }
+  float Ff[Q], J[NTRI], s[NM], bf[NM];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
+  gen::moments<float>(Ff, s, J);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) bf[k] = trunc_float(dl[k]);
+  const bool ok = ldlt_solve<float>(J, bf);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) dl[k] = exact_double(bf[k]);
   return ok;
 }
 
@@ -184,51 +234,55 @@ struct NewtonResult {
 
 // Newton-Raphson for the 13 multipliers (Sec. 3, Sec. 5 step table), from the
 // multipliers in `lam` (warm start or Gaussian cold start).  Reading of the
-// stopping rule: at least min_upd updates; stop when max|G| < tol, except
-// that a solve landing in [tol/100, tol) takes one more full (polishing)
-// step; while max|G| >= tol the step is halved until ||G||_2 decreases.
-// On return F holds exp(Phi lam) at the returned lam.
-template <int BLK>
-__device__ NewtonResult newton(WS<BLK> lam, WS<BLK> F, WS<BLK> m, const Phys& ph, int maxit) {
-  double l0[NM], G[NM];
+// stopping rule: stop when max|G| < tol, after at least min_upd updates,
+// except that a solve landing in [tol/100, tol) takes one more full
+// (polishing) step; while max|G| >= tol the step is halved until ||G||_2
+// decreases.  On return F holds exp(Phi lam) at the returned lam.
+// One evaluation site and one direction site keep the unrolled code small;
+// trial point and direction live in the workspace (w: the cell's workspace).
+template <int BLK, bool MIXED>
+__device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit) {
+  WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), lt = w.at(WS_LT),
+          dl = w.at(WS_DL);
 #pragma unroll
-  for (int k = 0; k < NM; ++k) l0[k] = lam[k];
-  eval_equilibrium<BLK>(l0, F, m, G);
-  int n = 0, failed = 0;
-  bool polished = false;
+  for (int k = 0; k < NM; ++k) lt[k] = lam[k];
+  int n = 0, failed = 0, ls = 0;
+  bool first = true, polished = false, restore = false;
+  double t = 0.0, s0 = 0.0;
   for (;;) {
+    double G[NM];
+    eval_equilibrium<BLK>(lt, F, m, G);
+    if (restore) break;  // F is back at the last accepted lam after a failed line search
+    if (!first && !polished && !(sum_sq(G) < s0)) {  // reject: halve the step
+      if (++ls > LS_MAX) {
+        failed = 1;
+        restore = true;
+#pragma unroll
+        for (int k = 0; k < NM; ++k) lt[k] = lam[k];
+        continue;
+      }
+      t *= 0.5;
+#pragma unroll
+      for (int k = 0; k < NM; ++k) lt[k] = fma(-t, dl[k], lam[k]);
+      continue;
+    }
+    // accept the trial point
+#pragma unroll
+    for (int k = 0; k < NM; ++k) lam[k] = lt[k];
+    if (!first) ++n;
+    first = false;
     const double r = max_abs(G);
     if (n >= ph.min_upd && r < ph.tol && (r < 1e-2 * ph.tol || polished)) break;
     if (n >= maxit) { failed = 1; break; }
-    const double s0 = sum_sq(G);
-    if (!jacobian_solve<BLK>(F, G)) { failed = 1; break; }  // G now holds delta
+    s0 = sum_sq(G);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) l0[k] = lam[k];
+    for (int k = 0; k < NM; ++k) dl[k] = G[k];
+    if (!newton_direction<BLK, MIXED>(F, dl)) { failed = 1; break; }
     polished = r < ph.tol;
-    double lt[NM], Gt[NM];
-    if (polished) {
+    t = 1.0;
+    ls = 0;
 #pragma unroll
-      for (int k = 0; k < NM; ++k) lt[k] = l0[k] - G[k];
-      eval_equilibrium<BLK>(lt, F, m, Gt);
-    } else {
-      double t = 1.0;
-      bool ok = false;
-      for (int ls = 0; ls <= LS_MAX; ++ls) {
-#pragma unroll
-        for (int k = 0; k < NM; ++k) lt[k] = fma(-t, G[k], l0[k]);
-        eval_equilibrium<BLK>(lt, F, m, Gt);
-        if (sum_sq(Gt) < s0) { ok = true; break; }
-        t *= 0.5;
-      }
-      if (!ok) {  // keep the last accepted point
-        eval_equilibrium<BLK>(l0, F, m, Gt);
-        failed = 1;
-        break;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NM; ++k) { lam[k] = lt[k]; G[k] = Gt[k]; }
-    ++n;
+    for (int k = 0; k < NM; ++k) lt[k] = lam[k] - dl[k];
   }
   return NewtonResult{n, failed};
 }
@@ -244,12 +298,11 @@ __device__ __forceinline__ void gaussian_guess(double ux, double uy, double uz, 
   for (int k = 0; k < NM; ++k) l[k] = 0.0;
   l[1] = ux * it; l[2] = uy * it; l[3] = uz * it;
   l[4] = l[5] = l[6] = -0.5 * it;
+  double e[Q];
+  gen::exponents(l, e);
   double s = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr int cx = CX[i], cy = CY[i], cz = CZ[i], cc = c2(i);
-    s += exp(l[1] * cx + l[2] * cy + l[3] * cz + l[4] * cc);
-  });
+#pragma unroll
+  for (int i = 0; i < Q; ++i) s += exp(e[i]);
   l[0] = -log(s);
 #pragma unroll
   for (int k = 0; k < NM; ++k) lam[k] = l[k];
@@ -263,54 +316,34 @@ __device__ __forceinline__ int alpha_branch(double eps) {
   return eps < 1e-2 ? 0 : eps < 1e-1 ? 1 : eps < 1.0 ? 2 : 3;
 }
 
+// True if an FP32 estimate s39 of 39*eps with absolute error below 2.5e-5
+// could lie on the other side of a threshold of Eq. (alpha) than the FP64 value.
+__device__ __forceinline__ bool near_threshold(float s39) {
+  constexpr float band = 5e-5f;
+  return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band ||
+         !(s39 == s39);
+}
+
 struct CellStats {
   int n_upd;
   int failed;
   int branch;
 };
 
-// One fluid-cell collision in FP64 (Sec. 3): f, g (post-streaming) in the
-// workspace -> moments -> targets -> Newton (warm start in lam) -> f^eq,
-// g^eq = (2C_v - D) T f^eq -> eps (f only) -> tau_eff = tau alpha(eps) ->
-// BGK on f and g, written back into the workspace.
-template <int BLK>
-__device__ CellStats collide_fp64(WS<BLK> w, const Phys& ph) {
-  WS<BLK> f = w.at(WS_F), g = w.at(WS_G), F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
-  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, e2 = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const double fi = f[i];
-    rho += fi;
-    constexpr int cx = CX[i], cy = CY[i], cz = CZ[i], cc = c2(i);
-    if constexpr (cx != 0) jx = fma((double)cx, fi, jx);
-    if constexpr (cy != 0) jy = fma((double)cy, fi, jy);
-    if constexpr (cz != 0) jz = fma((double)cz, fi, jz);
-    if constexpr (cc != 0) e2 = fma((double)cc, fi, e2);
-    e2 += g[i];
-  });
+// Macroscopic variables (Sec. 3): rho, u and T from the total energy,
+// sum f|xi|^2 + sum g = rho u^2 + 2 C_v rho T (E = u^2/2 + C_v T, Sec. 2).
+struct Macro {
+  double rho, ux, uy, uz, T;
+};
+
+__device__ __forceinline__ Macro macro_from_moments(double rho, double jx, double jy, double jz,
+                                                    double e2, double inv_2cv) {
   const double ir = 1.0 / rho;
-  const double ux = jx * ir, uy = jy * ir, uz = jz * ir;
-  const double T = (e2 - rho * (ux * ux + uy * uy + uz * uz)) * ph.inv_2cv * ir;
-  targets<BLK>(ux, uy, uz, T, m);
-  const NewtonResult nr = newton<BLK>(lam, F, m, ph, ph.maxit);
-  double eps = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const double feq = rho * F[i];
-    eps += fabs(f[i] - feq) / feq;
-  });
-  eps *= (1.0 / Q);
-  const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
-  const double omega = 1.0 / (ph.tau * alpha);
-  const double cgr = ph.cg * T * rho;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const double Fi = F[i];
-    const double fi = f[i], gi = g[i];
-    f[i] = fi - omega * (fi - rho * Fi);
-    g[i] = gi - omega * (gi - cgr * Fi);
-  });
-  return CellStats{nr.n_upd, nr.failed, alpha_branch(eps)};
+  Macro M;
+  M.rho = rho;
+  M.ux = jx * ir; M.uy = jy * ir; M.uz = jz * ir;
+  M.T = (e2 - rho * (M.ux * M.ux + M.uy * M.uy + M.uz * M.uz)) * inv_2cv * ir;
+  return M;
 }
 
 }  // namespace lbm39

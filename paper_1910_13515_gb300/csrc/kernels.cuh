@@ -2,17 +2,24 @@
 // fused collide-and-stream passes (AA pattern), boundary fills, macroscopic
 // read-out and conserved sums.
 //
-// Storage: 78 planes of Np elements (f_0..f_38 then g_0..g_38), x fastest.
+// Storage: 78 planes of Np elements (f_0..f_38 then g_0..g_38), x fastest,
+// of type P: double (FP64 path) or float (precision form: each population
+// stored as its deviation from a reference population h_ref, Desc::href).
 // AA pattern over one buffer.  At even time the buffer holds the
 // pre-collision populations h_i(x) in slot (x, i).  The even pass reads its
 // own slots, collides and writes h*_i(x) into slot (x, opp i).  The odd pass
 // gathers h_i(x) = h*_i(x - xi_i) from slot (x - xi_i, opp i), collides and
 // pushes h*_i(x) into slot (x + xi_i, i), which is the pre-collision h_i of
-// the next time step.  Every slot is read and written by one thread only.
-// Half-way bounce-back: a source (odd gather) or destination (odd push) that
-// is solid redirects to the cell's own slot of the opposite direction.
+// the next time step.  Every slot is read and written by one thread only (the
+// slot pushed for direction i is the one gathered for opp(i)).  Half-way
+// bounce-back: a source (odd gather) or destination (odd push) that is solid
+// redirects to the cell's own slot of the opposite direction; the per-cell
+// bit set Desc::bounce marks the directions whose source is solid.
 // Freestream and outflow cells never collide; the fill kernels give the
 // fluid cells what those cells would have streamed (Sec. 4 boundary kinds).
+//
+// A fluid cell's step runs in three phases: gather and moments; targets and
+// Newton (F, lam, m in shared memory); gather again, sensor, BGK and push.
 #pragma once
 #include <cstdint>
 
@@ -21,14 +28,18 @@
 namespace lbm39 {
 
 struct Desc {
-  double* pop;                 // 78 planes
-  double* lam;                 // 13 planes, multipliers kept between steps
-  const uint8_t* mask;         // nullptr: every cell fluid, all axes periodic
-  unsigned long long* ctr;     // counters (see CTR_*)
-  const double* heq_inf;       // 78 far-field equilibrium populations
-  long long N, Np;             // cells, plane stride in elements
+  void* pop;                          // 78 planes of P
+  double* lam;                        // 13 planes, multipliers kept between steps
+  const uint8_t* mask;                // nullptr: every cell fluid, all axes periodic
+  const unsigned long long* bounce;   // bit i: the source x - xi_i is solid (nullptr: none)
+  unsigned long long* ctr;            // counters (CTR_*)
+  const void* free_store;             // 78 stored values (P) of a freestream cell
+  const double* heq_inf;              // 78 far-field equilibrium populations (FP64)
+  const double* href;                 // 78 reference populations (precision form)
+  double mref[5];                     // sum of href: rho, j, sum f|xi|^2 + sum g
+  long long N, Np;                    // cells, plane stride in elements
   int nx, ny, nz;
-  int per[3];                  // periodic axes
+  int per[3];                         // periodic axes
   Phys ph;
 };
 
@@ -53,6 +64,7 @@ __device__ __forceinline__ int wrap(int a, int n) {
 struct Nbr {
   int xs[7];
   long long ys[7], zs[7];
+  __device__ __forceinline__ Nbr() {}
   __device__ __forceinline__ Nbr(const Desc& d, Coord c) {
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
@@ -66,52 +78,171 @@ struct Nbr {
   }
 };
 
-// Pre-collision populations of fluid cell `cell` at the lattice's current time:
-// own slots at even time, the odd gather (with bounce-back) at odd time.
-template <bool ODD, int BLK>
-__device__ __forceinline__ void gather(const Desc& d, long long cell, WS<BLK> w) {
-  const double* __restrict__ P = d.pop;
-  if constexpr (!ODD) {
-    static_for<0, 2 * Q>([&](auto I) {
-      constexpr int j = decltype(I)::value;
-      w[j] = P[j * d.Np + cell];
-    });
-  } else {
-    const Nbr nb(d, coord_of(d, cell));
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
+// Pre-collision populations of one distribution (base 0: f, Q: g) of fluid
+// cell `cell` at the lattice's current time: own slots at even time, the odd
+// gather (with bounce-back) at odd time.
+template <bool ODD, class P>
+__device__ __forceinline__ void gather(const Desc& d, long long cell, const Nbr& nb,
+                                       unsigned long long bits, int base, P (&h)[Q]) {
+  const P* __restrict__ pop = static_cast<const P*>(d.pop);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (!ODD) {
+      h[i] = pop[(long long)(base + i) * d.Np + cell];
+    } else {
       constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
-      const long long s = nb.at(-cx, -cy, -cz);
-      const bool solid = d.mask != nullptr && d.mask[s] == MASK_SOLID;
-      const long long src = solid ? (long long)i * d.Np + cell : (long long)opp(i) * d.Np + s;
-      w[WS_F + i] = P[src];
-      w[WS_G + i] = P[src + Q * d.Np];
-    });
+      const long long src = ((bits >> i) & 1ull)
+                                ? (long long)(base + i) * d.Np + cell
+                                : (long long)(base + opp(i)) * d.Np + nb.at(-cx, -cy, -cz);
+      h[i] = pop[src];
+    }
+  });
+}
+
+// Post-collision population h*_i of fluid cell `cell` into its AA slot.
+template <bool ODD, class P, int i>
+__device__ __forceinline__ void push(const Desc& d, long long cell, const Nbr& nb,
+                                     unsigned long long bits, int base, P v) {
+  P* __restrict__ pop = static_cast<P*>(d.pop);
+  if constexpr (!ODD) {
+    pop[(long long)(base + opp(i)) * d.Np + cell] = v;
+  } else {
+    constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
+    const long long dst = ((bits >> opp(i)) & 1ull)
+                              ? (long long)(base + opp(i)) * d.Np + cell
+                              : (long long)(base + i) * d.Np + nb.at(cx, cy, cz);
+    pop[dst] = v;
   }
 }
 
-// Post-collision populations of fluid cell `cell` into their AA slots.
-template <bool ODD, int BLK>
-__device__ __forceinline__ void scatter(const Desc& d, long long cell, WS<BLK> w) {
-  double* __restrict__ P = d.pop;
-  if constexpr (!ODD) {
+// Raw moments of a cell: rho, j = rho u, e2 = sum f|xi|^2 + sum g = 2 rho E.
+struct Raw {
+  double rho, jx, jy, jz, e2;
+};
+
+// Phase A: gather each distribution in turn and take the moments (FP64).
+template <bool ODD, class P>
+__device__ __forceinline__ Raw gather_raw(const Desc& d, long long cell, const Nbr& nb,
+                                          unsigned long long bits) {
+  Raw r;
+  double gs;
+  if constexpr (sizeof(P) == 8) {
+    P h[Q];
+    gather<ODD, P>(d, cell, nb, bits, 0, h);
+    gen::f_moments<double>(h, r.rho, r.jx, r.jy, r.jz, r.e2);
+    gather<ODD, P>(d, cell, nb, bits, Q, h);
+    gs = gen::g_sum<double>(h);
+  } else {  // deviations: moments of h_ref (precomputed) plus those of the deviations
+    P h[Q];
+    double hd[Q];
+    gather<ODD, P>(d, cell, nb, bits, 0, h);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
+    gen::f_moments<double>(hd, r.rho, r.jx, r.jy, r.jz, r.e2);
+    gather<ODD, P>(d, cell, nb, bits, Q, h);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
+    gs = gen::g_sum<double>(hd);
+    r.rho += d.mref[0]; r.jx += d.mref[1]; r.jy += d.mref[2]; r.jz += d.mref[3];
+    gs += d.mref[4];
+  }
+  r.e2 += gs;
+  return r;
+}
+
+template <bool ODD, class P>
+__device__ __forceinline__ Macro gather_moments(const Desc& d, long long cell, const Nbr& nb,
+                                                unsigned long long bits) {
+  const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+  return macro_from_moments(r.rho, r.jx, r.jy, r.jz, r.e2, d.ph.inv_2cv);
+}
+
+// Round-to-nearest double -> float by integer operations (normal range;
+// other values take the conversion instruction).
+__device__ __forceinline__ float round_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long r = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
+  const int e = (int)((r >> 52) & 0x7ff) - 896;
+  if (e <= 0 || e >= 255) return __double2float_rn(x);
+  return __uint_as_float((unsigned)((b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
+                         (unsigned)((r >> 29) & 0x7fffffu));
+}
+
+// Phase C: gather again, Knudsen sensor (Eq. DeltaAvg, f only), tau_eff =
+// tau alpha(eps) (Eq. alpha) for f and g, BGK and push.  F holds the final
+// normalised equilibrium; f^eq = rho F, g^eq = (2C_v - D) T rho F.
+template <bool ODD, class P, int BLK>
+__device__ __forceinline__ int relax_push(const Desc& d, long long cell, const Nbr& nb,
+                                          unsigned long long bits, const Macro& M, WS<BLK> F) {
+  const Phys& ph = d.ph;
+  const double rho = M.rho;
+  const float rho32 = trunc_float(rho);
+  const double cgr = ph.cg * M.T * rho;
+  double eps;
+  if constexpr (sizeof(P) == 8) {
+    P f[Q];
+    gather<ODD, P>(d, cell, nb, bits, 0, f);
+    // FP32 estimate of 39 eps from float views (absolute error < 2.5e-5),
+    // FP64 value when that cannot decide the branch of Eq. (alpha)
+    float s32 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float feq = rho32 * trunc_float(F[i]);
+      s32 += fabsf(trunc_float(f[i]) - feq) / feq;
+    }
+    eps = (double)s32 * (1.0 / Q);
+    if (near_threshold(s32)) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double feq = rho * F[i];
+        s += fabs(f[i] - feq) / feq;
+      }
+      eps = s * (1.0 / Q);
+    }
+    const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
+    const double omega = 1.0 / (ph.tau * alpha);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      P[(long long)opp(i) * d.Np + cell] = w[WS_F + i];
-      P[(long long)(Q + opp(i)) * d.Np + cell] = w[WS_G + i];
+      push<ODD, P, i>(d, cell, nb, bits, 0, fma(-omega, fma(-rho, F[i], f[i]), f[i]));
+    });
+    P g[Q];
+    gather<ODD, P>(d, cell, nb, bits, Q, g);
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      push<ODD, P, i>(d, cell, nb, bits, Q, fma(-omega, fma(-cgr, F[i], g[i]), g[i]));
     });
   } else {
-    const Nbr nb(d, coord_of(d, cell));
+    // precision form: h~ = h - h_ref stored in FP32; equilibrium deviation
+    // h^eq - h_ref formed in FP64 and rounded; sensor and BGK in FP32.
+    const double* __restrict__ href = d.href;
+    P f[Q];
+    gather<ODD, P>(d, cell, nb, bits, 0, f);
+    float s32 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double Fi = F[i];
+      f[i] -= round_float(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
+      s32 += fabsf(f[i]) / (rho32 * trunc_float(Fi));
+    }
+    eps = (double)s32 * (1.0 / Q);
+    const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
+    const float omega = (float)(1.0 / (ph.tau * alpha));
+    P f2[Q];
+    gather<ODD, P>(d, cell, nb, bits, 0, f2);  // the stored values again (cached)
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
-      const long long t = nb.at(cx, cy, cz);
-      const bool solid = d.mask != nullptr && d.mask[t] == MASK_SOLID;
-      const long long dst = solid ? (long long)opp(i) * d.Np + cell : (long long)i * d.Np + t;
-      P[dst] = w[WS_F + i];
-      P[dst + Q * d.Np] = w[WS_G + i];
+      push<ODD, P, i>(d, cell, nb, bits, 0, fmaf(-omega, f[i], f2[i]));
+    });
+    P g[Q];
+    gather<ODD, P>(d, cell, nb, bits, Q, g);
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const float qg = round_float(fma(cgr, F[i], -__ldg(href + Q + i)));
+      push<ODD, P, i>(d, cell, nb, bits, Q, fmaf(-omega, g[i] - qg, g[i]));
     });
   }
+  return alpha_branch(eps);
 }
 
 template <int BLK>
@@ -122,45 +253,60 @@ __device__ __forceinline__ void flush_stats(unsigned int* s_ctr, unsigned long l
 }
 
 // One time step over every fluid cell (even or odd AA pass).
-template <bool ODD, int BLK>
+template <bool ODD, class P, int BLK>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
   for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
-  __syncthreads();
+  load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
-  const bool active =
-      cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID);
+  const bool active = cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID);
   if (active) {
     WS<BLK> w{smem + threadIdx.x};
-    gather<ODD, BLK>(d, cell, w);
+    WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
+    Nbr nb;
+    unsigned long long bits = 0;
+    if constexpr (ODD) {
+      nb = Nbr(d, coord_of(d, cell));
+      if (d.bounce) bits = d.bounce[cell];
+    }
+    const Macro M = gather_moments<ODD, P>(d, cell, nb, bits);
+    targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) w[WS_LAM + k] = d.lam[k * d.Np + cell];
-    const CellStats cs = collide_fp64<BLK>(w, d.ph);
+    for (int k = 0; k < NM; ++k) lam[k] = d.lam[k * d.Np + cell];
+    const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = w[WS_LAM + k];
-    scatter<ODD, BLK>(d, cell, w);
-    atomicAdd(&s_ctr[CTR_FAILED], (unsigned)cs.failed);
-    atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)cs.n_upd);
-    atomicAdd(&s_ctr[CTR_HIST + min(cs.n_upd, 31)], 1u);
-    atomicAdd(&s_ctr[CTR_EPS + cs.branch], 1u);
+    for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
+    const int branch = relax_push<ODD, P, BLK>(d, cell, nb, bits, M, F);
+    atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
+    atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
+    atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
+    atomicAdd(&s_ctr[CTR_EPS + branch], 1u);
   }
   flush_stats<BLK>(s_ctr, d.ctr);
+}
+
+// Stored value of population j (0..77) whose FP64 value is v.
+template <class P>
+__device__ __forceinline__ P to_store(const Desc& d, int j, double v) {
+  if constexpr (sizeof(P) == 8) return v;
+  else return round_float(v - __ldg(d.href + j));
 }
 
 // Equilibrium initial condition of fluid cells in [c0, c0 + len): inputs are
 // indexed by cell - c0; u planes are `us` elements apart.  Non-fluid cells in
 // the range get zero populations and multipliers.
-template <int BLK>
+template <class P, int BLK>
 __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const double* u,
                                               long long us, const double* T, long long c0,
                                               long long len, int maxit) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
   for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
-  __syncthreads();
+  load_exp_table();
   const long long r = (long long)blockIdx.x * BLK + threadIdx.x;
   const long long cell = c0 + r;
+  P* pop = static_cast<P*>(d.pop);
   if (r < len && cell < d.N) {
     const bool fluid = d.mask == nullptr || d.mask[cell] == MASK_FLUID;
     WS<BLK> w{smem + threadIdx.x};
@@ -169,18 +315,17 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
       WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
       targets<BLK>(ux, uy, uz, TT, m);
       gaussian_guess<BLK>(ux, uy, uz, TT, lam);
-      const NewtonResult nr = newton<BLK>(lam, F, m, d.ph, maxit);
+      const NewtonResult nr = newton<BLK, false>(w, d.ph, maxit);
       const double cgr = d.ph.cg * TT * rr;
-      static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        d.pop[(long long)i * d.Np + cell] = rr * F[i];
-        d.pop[(long long)(Q + i) * d.Np + cell] = cgr * F[i];
-      });
+      for (int i = 0; i < Q; ++i) {
+        pop[(long long)i * d.Np + cell] = to_store<P>(d, i, rr * F[i]);
+        pop[(long long)(Q + i) * d.Np + cell] = to_store<P>(d, Q + i, cgr * F[i]);
+      }
 #pragma unroll
       for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
       atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
     } else {
-      for (int j = 0; j < 2 * Q; ++j) d.pop[(long long)j * d.Np + cell] = 0.0;
+      for (int j = 0; j < 2 * Q; ++j) pop[(long long)j * d.Np + cell] = P(0);
       for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = 0.0;
     }
   }
@@ -188,19 +333,21 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
 }
 
 // Equilibrium populations (f then g, 78 values) and multipliers of one state
-// (rho, u, T), from a cold start; one thread.  Used for the far-field state.
+// (rho, u, T), from a cold start; one thread.  Used for the far-field state
+// and for the reference state of the precision form.
 template <int BLK>
 __global__ void __launch_bounds__(BLK) k_state_equilibrium(Phys ph, double rho, double ux,
                                                            double uy, double uz, double T,
                                                            double* out78, int maxit,
                                                            unsigned long long* failed) {
   extern __shared__ double smem[];
+  load_exp_table();
   if (threadIdx.x != 0) return;
   WS<BLK> w{smem};
   WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
   targets<BLK>(ux, uy, uz, T, m);
   gaussian_guess<BLK>(ux, uy, uz, T, lam);
-  const NewtonResult nr = newton<BLK>(lam, F, m, ph, maxit);
+  const NewtonResult nr = newton<BLK, false>(w, ph, maxit);
   for (int i = 0; i < Q; ++i) {
     out78[i] = rho * F[i];
     out78[Q + i] = ph.cg * T * rho * F[i];
@@ -208,14 +355,30 @@ __global__ void __launch_bounds__(BLK) k_state_equilibrium(Phys ph, double rho, 
   if (nr.failed) atomicAdd(failed, 1ull);
 }
 
+// Bit i of bounce[cell]: the source x - xi_i of fluid cell `cell` is solid.
+__global__ void k_bounce_bits(Desc d, unsigned long long* bounce) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= d.N) return;
+  unsigned long long b = 0;
+  if (d.mask[cell] == MASK_FLUID) {
+    const Nbr nb(d, coord_of(d, cell));
+    for (int i = 0; i < Q; ++i)
+      if (d.mask[nb.at(-kCX[i], -kCY[i], -kCZ[i])] == MASK_SOLID) b |= 1ull << i;
+  }
+  bounce[cell] = b;
+}
+
 // After an even pass: freestream cells hold the far-field post-collision
 // populations and outflow cells a copy of the cell with x clamped into
 // [3, nx-4], both in the reversed (post-collision) layout the odd pass reads.
+template <class P>
 __global__ void k_fill_even(Desc d) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= d.N) return;
   const uint8_t mk = d.mask[cell];
   if (mk != MASK_FREE && mk != MASK_OUT) return;
+  P* pop = static_cast<P*>(d.pop);
+  const P* fs = static_cast<const P*>(d.free_store);
   long long src = -1;
   if (mk == MASK_OUT) {
     const Coord c = coord_of(d, cell);
@@ -226,11 +389,11 @@ __global__ void k_fill_even(Desc d) {
   for (int i = 0; i < Q; ++i) {
     const long long jf = (long long)opp(i) * d.Np, jg = (long long)(Q + opp(i)) * d.Np;
     if (src < 0) {
-      d.pop[jf + cell] = d.heq_inf[i];
-      d.pop[jg + cell] = d.heq_inf[Q + i];
+      pop[jf + cell] = fs[i];
+      pop[jg + cell] = fs[Q + i];
     } else {
-      d.pop[jf + cell] = d.pop[jf + src];
-      d.pop[jg + cell] = d.pop[jg + src];
+      pop[jf + cell] = pop[jf + src];
+      pop[jg + cell] = pop[jg + src];
     }
   }
 }
@@ -239,6 +402,7 @@ __global__ void k_fill_even(Desc d) {
 // receive what that cell streamed: the far-field equilibrium, or the
 // post-collision population of the clamped cell c (which c pushed into
 // slot (c + xi_i, i), or bounced into (c, opp i) if c + xi_i is solid).
+template <class P>
 __global__ void k_fill_odd(Desc d) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= d.N || d.mask[cell] != MASK_FLUID) return;
@@ -247,6 +411,8 @@ __global__ void k_fill_odd(Desc d) {
                     (!d.per[1] && (c.y < 6 || c.y >= d.ny - 6)) ||
                     (!d.per[2] && (c.z < 6 || c.z >= d.nz - 6));
   if (!near) return;
+  P* pop = static_cast<P*>(d.pop);
+  const P* fs = static_cast<const P*>(d.free_store);
   const Nbr nb(d, c);
   for (int i = 0; i < Q; ++i) {
     const long long s = nb.at(-kCX[i], -kCY[i], -kCZ[i]);
@@ -267,82 +433,61 @@ __global__ void k_fill_odd(Desc d) {
       }
     }
     if (src < 0) {
-      d.pop[jf + cell] = d.heq_inf[i];
-      d.pop[jg + cell] = d.heq_inf[Q + i];
+      pop[jf + cell] = fs[i];
+      pop[jg + cell] = fs[Q + i];
     } else {
-      d.pop[jf + cell] = d.pop[src];
-      d.pop[jg + cell] = d.pop[src + Q * d.Np];
+      pop[jf + cell] = pop[src];
+      pop[jg + cell] = pop[src + Q * d.Np];
     }
   }
 }
 
-// Moments of one cell's pre-collision populations: rho, u, T (total energy).
-template <int BLK>
-__device__ __forceinline__ void cell_macros(WS<BLK> w, double cv2inv, double& rho, double& ux,
-                                            double& uy, double& uz, double& T) {
-  double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, e2 = 0.0;
-  static_for<0, Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const double fi = w[WS_F + i];
-    r += fi;
-    constexpr int cx = CX[i], cy = CY[i], cz = CZ[i], cc = c2(i);
-    if constexpr (cx != 0) jx = fma((double)cx, fi, jx);
-    if constexpr (cy != 0) jy = fma((double)cy, fi, jy);
-    if constexpr (cz != 0) jz = fma((double)cz, fi, jz);
-    if constexpr (cc != 0) e2 = fma((double)cc, fi, e2);
-    e2 += w[WS_G + i];
-  });
-  const double ir = 1.0 / r;
-  rho = r;
-  ux = jx * ir; uy = jy * ir; uz = jz * ir;
-  T = (e2 - r * (ux * ux + uy * uy + uz * uz)) * cv2inv * ir;
-}
-
 // rho, u, T, p = rho T of cells [c0, c0 + len) into out arrays indexed by
 // cell - c0 (u planes `us` apart; any pointer may be null); non-fluid cells 0.
-template <bool ODD, int BLK>
-__global__ void __launch_bounds__(BLK) k_macros(Desc d, double* rho, double* u, long long us,
-                                                double* T, double* p, long long c0,
-                                                long long len) {
-  extern __shared__ double smem[];
-  const long long r = (long long)blockIdx.x * BLK + threadIdx.x;
+template <bool ODD, class P>
+__global__ void k_macros(Desc d, double* rho, double* u, long long us, double* T, double* p,
+                         long long c0, long long len) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long cell = c0 + r;
   if (r >= len || cell >= d.N) return;
-  double vr = 0, vx = 0, vy = 0, vz = 0, vT = 0;
+  Macro M{0, 0, 0, 0, 0};
   if (d.mask == nullptr || d.mask[cell] == MASK_FLUID) {
-    WS<BLK> w{smem + threadIdx.x};
-    gather<ODD, BLK>(d, cell, w);
-    cell_macros<BLK>(w, d.ph.inv_2cv, vr, vx, vy, vz, vT);
+    Nbr nb;
+    unsigned long long bits = 0;
+    if constexpr (ODD) {
+      nb = Nbr(d, coord_of(d, cell));
+      if (d.bounce) bits = d.bounce[cell];
+    }
+    M = gather_moments<ODD, P>(d, cell, nb, bits);
   }
-  if (rho) rho[r] = vr;
-  if (u) { u[r] = vx; u[us + r] = vy; u[2 * us + r] = vz; }
-  if (T) T[r] = vT;
-  if (p) p[r] = vr * vT;
+  if (rho) rho[r] = M.rho;
+  if (u) { u[r] = M.ux; u[us + r] = M.uy; u[2 * us + r] = M.uz; }
+  if (T) T[r] = M.T;
+  if (p) p[r] = M.rho * M.T;
 }
 
 // Conserved sums over fluid cells (mass, momentum, total energy): fixed
 // grid-stride assignment and fixed-order tree reductions, so the result is
 // deterministic.  partials: gridDim.x * 5 doubles.
-template <bool ODD, int BLK>
+template <bool ODD, class P, int BLK>
 __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
-  extern __shared__ double smem[];
   __shared__ double red[5][BLK];
   double acc[5] = {0, 0, 0, 0, 0};
-  WS<BLK> w{smem + threadIdx.x};
   for (long long cell = (long long)blockIdx.x * BLK + threadIdx.x; cell < d.N;
        cell += (long long)gridDim.x * BLK) {
     if (d.mask != nullptr && d.mask[cell] != MASK_FLUID) continue;
-    gather<ODD, BLK>(d, cell, w);
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const double fi = w[WS_F + i];
-      constexpr int cx = CX[i], cy = CY[i], cz = CZ[i], cc = c2(i);
-      acc[0] += fi;
-      acc[1] += cx * fi;
-      acc[2] += cy * fi;
-      acc[3] += cz * fi;
-      acc[4] += 0.5 * (cc * fi + w[WS_G + i]);
-    });
+    Nbr nb;
+    unsigned long long bits = 0;
+    if constexpr (ODD) {
+      nb = Nbr(d, coord_of(d, cell));
+      if (d.bounce) bits = d.bounce[cell];
+    }
+    const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+    acc[0] += r.rho;
+    acc[1] += r.jx;
+    acc[2] += r.jy;
+    acc[3] += r.jz;
+    acc[4] += 0.5 * r.e2;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = acc[k];
@@ -354,6 +499,16 @@ __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
     __syncthreads();
   }
   if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Library exponential and CUDA's exp side by side (diagnostic).
+__global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
+  load_exp_table();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    y[i] = exp_tang(x[i]);
+    ref[i] = exp(x[i]);
+  }
 }
 
 __global__ void k_sum_partials(const double* partials, int nblocks, double* out5) {

@@ -2,7 +2,8 @@
 //
 // The library owns no device memory: every buffer is the caller's.  Each call
 // validates its arguments, enqueues kernels on the lattice's stream and maps
-// CUDA errors to LBM39_ERR_CUDA.
+// CUDA errors to LBM39_ERR_CUDA.  Kernels are instantiated for the two
+// population storages: double (LBM39_FP64) and float deviations (LBM39_MIXED).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,16 +23,19 @@ namespace {
 constexpr int BLK = 64;                          // threads per block of the cell kernels
 constexpr size_t WS_BYTES = (size_t)BLK * WS_DOUBLES * sizeof(double);
 constexpr int RED_BLOCKS = 1024;                 // blocks of the conserved-sum reduction
+constexpr int RED_THREADS = 128;
 constexpr long long STAGE_CELLS = 1LL << 20;     // host staging chunk (cells)
 constexpr uint64_t CKPT_MAGIC = 0x3933424d4c424c31ull;
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct AuxLayout {
-  size_t lam, ctr, heq, partials, result, stage, total;
+  size_t lam, ctr, heq, href, fstore, bounce, partials, result, stage, total;
 };
 
-long long plane_stride(long long N) { return (N + 31) / 32 * 32; }
+long long plane_stride(long long N) { return (N + 63) / 64 * 64; }
+
+size_t pop_elem(int precision) { return precision == LBM39_MIXED ? sizeof(float) : sizeof(double); }
 
 AuxLayout aux_layout(long long N) {
   const long long Np = plane_stride(N);
@@ -40,6 +44,9 @@ AuxLayout aux_layout(long long N) {
   a.lam = off; off = align256(off + sizeof(double) * NM * Np);
   a.ctr = off; off = align256(off + sizeof(unsigned long long) * 64);
   a.heq = off; off = align256(off + sizeof(double) * 2 * Q);
+  a.href = off; off = align256(off + sizeof(double) * 2 * Q);
+  a.fstore = off; off = align256(off + sizeof(double) * 2 * Q);
+  a.bounce = off; off = align256(off + sizeof(unsigned long long) * Np);
   a.partials = off; off = align256(off + sizeof(double) * 5 * RED_BLOCKS);
   a.result = off; off = align256(off + sizeof(double) * 8);
   a.stage = off; off = align256(off + sizeof(double) * 6 * std::min(N, STAGE_CELLS));
@@ -56,7 +63,8 @@ bool params_ok(const lbm39_params* p) {
   if (p->newton_maxit < 1 || p->newton_maxit > 1000 || p->newton_min_upd < 0 ||
       p->init_maxit < 1 || p->init_maxit > 10000)
     return false;
-  if (p->precision != LBM39_FP64) return false;
+  if (p->precision != LBM39_FP64 && p->precision != LBM39_MIXED) return false;
+  if (p->precision == LBM39_MIXED && !(p->ref_rho > 0.0 && p->ref_T > 0.0)) return false;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? p->nx : a == 1 ? p->ny : p->nz;
     if (!p->periodic[a] && n < 7) return false;  // 3 boundary layers per end + fluid
@@ -74,12 +82,14 @@ struct lbm39_lattice {
   AuxLayout lay{};
   const uint8_t* mask = nullptr;
   bool ghosts = false;
+  bool mixed = false;
   cudaStream_t stream = nullptr;
   long long t = 0;
   bool initialized = false;
   Desc desc{};
   unsigned long long* ctr() { return reinterpret_cast<unsigned long long*>(aux + lay.ctr); }
   double* stage() { return reinterpret_cast<double*>(aux + lay.stage); }
+  size_t pop_bytes() const { return pop_elem(p.precision) * 2 * Q * Np; }
 };
 
 #define CUDA_OK(x)                                   \
@@ -89,21 +99,41 @@ struct lbm39_lattice {
 
 static int last_launch() { return cudaGetLastError() == cudaSuccess ? LBM39_OK : LBM39_ERR_CUDA; }
 
-static int set_smem_attrs() {
-  static bool done = false;
-  if (done) return LBM39_OK;
-  const int bytes = (int)WS_BYTES;
-  CUDA_OK(cudaFuncSetAttribute(k_step<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_step<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_init<BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_state_equilibrium<BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_macros<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_macros<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_conserved<false, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  CUDA_OK(cudaFuncSetAttribute(k_conserved<true, BLK>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done = true;
-  return LBM39_OK;
-}
+// Kernel launches for one storage type.
+template <class P>
+struct Launch {
+  static void step(lbm39_lattice* L, bool odd) {
+    const unsigned grid = (unsigned)((L->N + BLK - 1) / BLK);
+    const unsigned fgrid = (unsigned)((L->N + 255) / 256);
+    if (!odd) {
+      k_step<false, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (L->ghosts) k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+    } else {
+      k_step<true, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (L->ghosts) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+    }
+  }
+  static void init(lbm39_lattice* L, const double* rho, const double* u, long long us,
+                   const double* T, long long c0, long long len) {
+    const unsigned grid = (unsigned)((len + BLK - 1) / BLK);
+    k_init<P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, c0, len,
+                                                       L->p.init_maxit);
+  }
+  static void macros(lbm39_lattice* L, double* rho, double* u, long long us, double* T,
+                     double* p, long long c0, long long len) {
+    const unsigned grid = (unsigned)((len + 127) / 128);
+    if (L->t & 1)
+      k_macros<true, P><<<grid, 128, 0, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
+    else
+      k_macros<false, P><<<grid, 128, 0, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
+  }
+  static void conserved(lbm39_lattice* L, double* partials, unsigned grid) {
+    if (L->t & 1)
+      k_conserved<true, P, RED_THREADS><<<grid, RED_THREADS, 0, L->stream>>>(L->desc, partials);
+    else
+      k_conserved<false, P, RED_THREADS><<<grid, RED_THREADS, 0, L->stream>>>(L->desc, partials);
+  }
+};
 
 extern "C" {
 
@@ -117,7 +147,7 @@ void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->kn_sensor = 1;
   p->newton_tol = 1e-12;
   p->newton_maxit = 30;
-  p->newton_min_upd = 1;
+  p->newton_min_upd = 0;
   p->init_maxit = 200;
   p->precision = LBM39_FP64;
   p->ref_rho = 1.0; p->ref_T = 0.5;
@@ -135,9 +165,59 @@ int lbm39_velocities(int32_t* vel, double* w) {
 int lbm39_query_bytes(const lbm39_params* p, size_t* pop_bytes, size_t* aux_bytes) {
   if (!params_ok(p)) return LBM39_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (pop_bytes) *pop_bytes = sizeof(double) * 2 * Q * plane_stride(N);
+  if (pop_bytes) *pop_bytes = pop_elem(p->precision) * 2 * Q * plane_stride(N);
   if (aux_bytes) *aux_bytes = aux_layout(N).total;
   return LBM39_OK;
+}
+
+// Validates the mask on the host; counts fluid cells, notes boundary and solid cells.
+static int check_mask(const lbm39_params* p, const std::vector<uint8_t>& m, long long* fluid,
+                      bool* ghosts, bool* solids) {
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  *fluid = 0;
+  *ghosts = *solids = false;
+  for (long long c = 0; c < N; ++c) {
+    const int x = int(c % p->nx), y = int((c / p->nx) % p->ny),
+              z = int(c / ((long long)p->nx * p->ny));
+    const int q[3] = {x, y, z};
+    bool layer = false;
+    for (int a = 0; a < 3; ++a)
+      if (!p->periodic[a] && (q[a] < 3 || q[a] >= n[a] - 3)) layer = true;
+    const uint8_t v = m[c];
+    if (v > 3) return LBM39_ERR_MASK;
+    if (v == MASK_FLUID) {
+      if (layer) return LBM39_ERR_MASK;
+      ++*fluid;
+    }
+    if (v == MASK_SOLID) *solids = true;
+    if (v == MASK_FREE || v == MASK_OUT) {
+      if (!layer) return LBM39_ERR_MASK;
+      *ghosts = true;
+    }
+    if (v == MASK_OUT) {
+      if (p->periodic[0] || !(x < 3 || x >= p->nx - 3)) return LBM39_ERR_MASK;
+      const int xc = std::min(std::max(x, 3), p->nx - 4);
+      const uint8_t t = m[c + (xc - x)];
+      if (t != MASK_FLUID && t != MASK_FREE) return LBM39_ERR_MASK;
+    }
+  }
+  return LBM39_OK;
+}
+
+// Equilibrium populations of one state into dev78 (device) and host78.
+static int state_equilibrium(const Phys& ph, cudaStream_t s, double rho, const double* u,
+                             double T, int maxit, double* dev78, unsigned long long* dfail,
+                             double* host78) {
+  CUDA_OK(cudaMemsetAsync(dfail, 0, sizeof(unsigned long long), s));
+  k_state_equilibrium<BLK><<<1, BLK, WS_BYTES, s>>>(ph, rho, u[0], u[1], u[2], T, dev78, maxit,
+                                                     dfail);
+  if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
+  unsigned long long nf = 0;
+  CUDA_OK(cudaMemcpyAsync(host78, dev78, sizeof(double) * 2 * Q, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaMemcpyAsync(&nf, dfail, sizeof nf, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  return nf ? LBM39_ERR_NEWTON : LBM39_OK;
 }
 
 int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, void* pop_buf,
@@ -157,38 +237,14 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   if (!mask_dev && !all_periodic) return LBM39_ERR_MASK;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   long long fluid = N;
-  bool ghosts = false;
+  bool ghosts = false, solids = false;
   if (mask_dev) {
     std::vector<uint8_t> m(N);
     CUDA_OK(cudaMemcpyAsync(m.data(), mask_dev, N, cudaMemcpyDeviceToHost, stream));
     CUDA_OK(cudaStreamSynchronize(stream));
-    fluid = 0;
-    const int n[3] = {p->nx, p->ny, p->nz};
-    for (long long c = 0; c < N; ++c) {
-      const int x = int(c % p->nx), y = int((c / p->nx) % p->ny), z = int(c / ((long long)p->nx * p->ny));
-      const int q[3] = {x, y, z};
-      bool layer = false;
-      for (int a = 0; a < 3; ++a)
-        if (!p->periodic[a] && (q[a] < 3 || q[a] >= n[a] - 3)) layer = true;
-      const uint8_t v = m[c];
-      if (v > 3) return LBM39_ERR_MASK;
-      if (v == MASK_FLUID) {
-        if (layer) return LBM39_ERR_MASK;
-        ++fluid;
-      }
-      if (v == MASK_FREE || v == MASK_OUT) {
-        if (!layer) return LBM39_ERR_MASK;
-        ghosts = true;
-      }
-      if (v == MASK_OUT) {
-        if (p->periodic[0] || !(x < 3 || x >= p->nx - 3)) return LBM39_ERR_MASK;
-        const int xc = std::min(std::max(x, 3), p->nx - 4);
-        const uint8_t t = m[c + (xc - x)];
-        if (t != MASK_FLUID && t != MASK_FREE) return LBM39_ERR_MASK;
-      }
-    }
+    const int rc = check_mask(p, m, &fluid, &ghosts, &solids);
+    if (rc) return rc;
   }
-  if (set_smem_attrs() != LBM39_OK) return LBM39_ERR_CUDA;
   lbm39_lattice* L = new (std::nothrow) lbm39_lattice;
   if (!L) return LBM39_ERR_ARG;
   L->p = *p;
@@ -200,13 +256,17 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   L->lay = aux_layout(N);
   L->mask = mask_dev;
   L->ghosts = ghosts;
+  L->mixed = p->precision == LBM39_MIXED;
   L->stream = stream;
   Desc& d = L->desc;
-  d.pop = static_cast<double*>(pop_buf);
+  d.pop = pop_buf;
   d.lam = reinterpret_cast<double*>(L->aux + L->lay.lam);
   d.mask = mask_dev;
+  d.bounce = nullptr;
   d.ctr = L->ctr();
   d.heq_inf = reinterpret_cast<const double*>(L->aux + L->lay.heq);
+  d.href = reinterpret_cast<const double*>(L->aux + L->lay.href);
+  d.free_store = L->aux + L->lay.fstore;
   d.N = N;
   d.Np = L->Np;
   d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
@@ -219,40 +279,60 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   d.ph.maxit = p->newton_maxit;
   d.ph.min_upd = p->newton_min_upd;
   d.ph.kn_sensor = p->kn_sensor ? 1 : 0;
-  // far-field equilibrium for freestream cells (counts failures in ctr[CTR_N])
-  unsigned long long* fail_slot = L->ctr() + CTR_N;
-  if (cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, stream) != cudaSuccess) {
-    delete L;
-    return LBM39_ERR_CUDA;
+  int rc = LBM39_OK;
+  // reference populations of the precision form and their moments
+  double href[2 * Q] = {0}, heq[2 * Q] = {0};
+  unsigned long long* dfail = L->ctr() + CTR_N;
+  if (L->mixed) {
+    const double u0[3] = {0, 0, 0};
+    rc = state_equilibrium(d.ph, stream, p->ref_rho, u0, p->ref_T, p->init_maxit,
+                           reinterpret_cast<double*>(L->aux + L->lay.href), dfail, href);
+    if (rc) { delete L; return rc; }
+    for (int k = 0; k < 5; ++k) d.mref[k] = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      d.mref[0] += href[i];
+      d.mref[1] += CX[i] * href[i];
+      d.mref[2] += CY[i] * href[i];
+      d.mref[3] += CZ[i] * href[i];
+      d.mref[4] += (CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i]) * href[i] + href[Q + i];
+    }
   }
-  k_state_equilibrium<BLK><<<1, BLK, WS_BYTES, stream>>>(
-      d.ph, p->rho_inf, p->u_inf[0], p->u_inf[1], p->u_inf[2], p->T_inf,
-      reinterpret_cast<double*>(L->aux + L->lay.heq), p->init_maxit, fail_slot);
-  unsigned long long nfail = 0;
-  if (last_launch() != LBM39_OK ||
-      cudaMemcpyAsync(&nfail, fail_slot, sizeof nfail, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-      cudaStreamSynchronize(stream) != cudaSuccess) {
-    delete L;
-    return LBM39_ERR_CUDA;
+  // far-field equilibrium for freestream cells, in the stored representation
+  if (ghosts) {
+    rc = state_equilibrium(d.ph, stream, p->rho_inf, p->u_inf, p->T_inf, p->init_maxit,
+                           reinterpret_cast<double*>(L->aux + L->lay.heq), dfail, heq);
+    if (rc) { delete L; return rc; }
+    if (L->mixed) {
+      float fs[2 * Q];
+      for (int j = 0; j < 2 * Q; ++j) fs[j] = (float)(heq[j] - href[j]);
+      if (cudaMemcpyAsync(L->aux + L->lay.fstore, fs, sizeof fs, cudaMemcpyHostToDevice, stream) !=
+          cudaSuccess) { delete L; return LBM39_ERR_CUDA; }
+    } else if (cudaMemcpyAsync(L->aux + L->lay.fstore, heq, sizeof heq, cudaMemcpyHostToDevice,
+                               stream) != cudaSuccess) {
+      delete L;
+      return LBM39_ERR_CUDA;
+    }
   }
-  if (ghosts && nfail) {
-    delete L;
-    return LBM39_ERR_NEWTON;
+  if (solids) {
+    unsigned long long* b = reinterpret_cast<unsigned long long*>(L->aux + L->lay.bounce);
+    k_bounce_bits<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(d, b);
+    if (last_launch() != LBM39_OK) { delete L; return LBM39_ERR_CUDA; }
+    d.bounce = b;
   }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) { delete L; return LBM39_ERR_CUDA; }
   *out = L;
   return LBM39_OK;
 }
 
 static int init_range(lbm39_lattice* L, const double* rho, const double* u, long long us,
                       const double* T, long long c0, long long len) {
-  const unsigned grid = (unsigned)((len + BLK - 1) / BLK);
-  k_init<BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, c0, len,
-                                                  L->p.init_maxit);
+  if (L->mixed) Launch<float>::init(L, rho, u, us, T, c0, len);
+  else Launch<double>::init(L, rho, u, us, T, c0, len);
   return last_launch();
 }
 
 static int init_begin(lbm39_lattice* L) {
-  CUDA_OK(cudaMemsetAsync(L->pop, 0, sizeof(double) * 2 * Q * L->Np, L->stream));
+  CUDA_OK(cudaMemsetAsync(L->pop, 0, L->pop_bytes(), L->stream));
   CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));
   L->t = 0;
   L->initialized = true;
@@ -289,16 +369,9 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
 int lbm39_step(lbm39_lattice* L, int64_t nsteps) {
   if (!L || nsteps < 0) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
-  const unsigned grid = (unsigned)((L->N + BLK - 1) / BLK);
-  const unsigned fgrid = (unsigned)((L->N + 255) / 256);
   for (int64_t s = 0; s < nsteps; ++s) {
-    if ((L->t & 1) == 0) {
-      k_step<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
-      if (L->ghosts) k_fill_even<<<fgrid, 256, 0, L->stream>>>(L->desc);
-    } else {
-      k_step<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
-      if (L->ghosts) k_fill_odd<<<fgrid, 256, 0, L->stream>>>(L->desc);
-    }
+    if (L->mixed) Launch<float>::step(L, L->t & 1);
+    else Launch<double>::step(L, L->t & 1);
     if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
     ++L->t;
   }
@@ -335,11 +408,8 @@ int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells) {
 
 static int read_range(lbm39_lattice* L, double* rho, double* u, long long us, double* T,
                       double* p, long long c0, long long len) {
-  const unsigned grid = (unsigned)((len + BLK - 1) / BLK);
-  if (L->t & 1)
-    k_macros<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
-  else
-    k_macros<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, rho, u, us, T, p, c0, len);
+  if (L->mixed) Launch<float>::macros(L, rho, u, us, T, p, c0, len);
+  else Launch<double>::macros(L, rho, u, us, T, p, c0, len);
   return last_launch();
 }
 
@@ -376,11 +446,10 @@ int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
   if (!L->initialized) return LBM39_ERR_STATE;
   double* partials = reinterpret_cast<double*>(L->aux + L->lay.partials);
   double* result = reinterpret_cast<double*>(L->aux + L->lay.result);
-  const unsigned grid = (unsigned)std::min<long long>(RED_BLOCKS, (L->N + BLK - 1) / BLK);
-  if (L->t & 1)
-    k_conserved<true, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, partials);
-  else
-    k_conserved<false, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc, partials);
+  const unsigned grid =
+      (unsigned)std::min<long long>(RED_BLOCKS, (L->N + RED_THREADS - 1) / RED_THREADS);
+  if (L->mixed) Launch<float>::conserved(L, partials, grid);
+  else Launch<double>::conserved(L, partials, grid);
   k_sum_partials<<<1, 32, 0, L->stream>>>(partials, (int)grid, result);
   if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
   unsigned long long c[CTR_N];
@@ -401,7 +470,7 @@ int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
 
 size_t lbm39_checkpoint_bytes(const lbm39_lattice* L) {
   if (!L) return 0;
-  return 256 + sizeof(double) * 2 * Q * L->Np + sizeof(double) * NM * L->Np;
+  return 256 + L->pop_bytes() + sizeof(double) * NM * L->Np;
 }
 
 int lbm39_save(lbm39_lattice* L, void* buf) {
@@ -413,7 +482,7 @@ int lbm39_save(lbm39_lattice* L, void* buf) {
   hdr[2] = (uint64_t)L->N;
   hdr[3] = (uint64_t)L->p.precision;
   char* b = static_cast<char*>(buf);
-  const size_t pb = sizeof(double) * 2 * Q * L->Np, lb = sizeof(double) * NM * L->Np;
+  const size_t pb = L->pop_bytes(), lb = sizeof(double) * NM * L->Np;
   CUDA_OK(cudaMemcpyAsync(b, hdr, sizeof hdr, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(b + 256, L->pop, pb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(b + 256 + pb, L->desc.lam, lb, cudaMemcpyDefault, L->stream));
@@ -429,7 +498,7 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   CUDA_OK(cudaStreamSynchronize(L->stream));
   if (hdr[0] != CKPT_MAGIC || hdr[2] != (uint64_t)L->N || hdr[3] != (uint64_t)L->p.precision)
     return LBM39_ERR_ARG;
-  const size_t pb = sizeof(double) * 2 * Q * L->Np, lb = sizeof(double) * NM * L->Np;
+  const size_t pb = L->pop_bytes(), lb = sizeof(double) * NM * L->Np;
   CUDA_OK(cudaMemcpyAsync(L->pop, b + 256, pb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(L->desc.lam, b + 256 + pb, lb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));
@@ -437,6 +506,14 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   L->t = (long long)hdr[1];
   L->initialized = true;
   return LBM39_OK;
+}
+
+int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void* cuda_stream) {
+  if (!x || !y || !ref || n < 0) return LBM39_ERR_ARG;
+  if (n == 0) return LBM39_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  k_selftest_exp<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, y, ref, n);
+  return last_launch();
 }
 
 void lbm39_destroy(lbm39_lattice* L) { delete L; }

@@ -88,6 +88,7 @@ def _load():
         "lbm39_checkpoint_bytes": (sz, [vp]),
         "lbm39_save": (i, [vp, vp]),
         "lbm39_load": (i, [vp, vp]),
+        "lbm39_selftest_exp": (i, [vp, vp, vp, i64, vp]),
         "lbm39_destroy": (None, [vp]),
         "lbm39_strerror": (ctypes.c_char_p, [i]),
     }
@@ -173,6 +174,10 @@ def lbm39_save(h, buf) -> int:
 
 def lbm39_load(h, buf) -> int:
     return _lib.lbm39_load(h, buf)
+
+
+def lbm39_selftest_exp(x, y, ref, n: int, stream) -> int:
+    return _lib.lbm39_selftest_exp(x, y, ref, n, stream)
 
 
 def lbm39_destroy(h) -> None:

@@ -45,7 +45,7 @@ def patch_from_checkpoint(L, buf, cx, cy, cz, r=3):
     p = L.params
     nx, ny, nz = p.nx, p.ny, p.nz
     N = nx * ny * nz
-    Np = (N + 31) // 32 * 32
+    Np = (N + 63) // 64 * 64
     body = buf[256:].view(torch.float64)
     pops = body[: 78 * Np].view(78, Np)
     lams = body[78 * Np: 78 * Np + 13 * Np].view(13, Np)

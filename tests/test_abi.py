@@ -51,11 +51,11 @@ def test_velocity_table_matches_the_paper_set_and_oracle(C, oracle):
 def test_default_params_and_sizes(C):
     p = C.lbm39_default_params(10, 8, 6)
     assert (p.nx, p.ny, p.nz) == (10, 8, 6) and list(p.periodic) == [1, 1, 1]
-    assert p.gamma == 1.4 and p.newton_tol == 1e-12 and p.newton_min_upd == 1
+    assert p.gamma == 1.4 and p.newton_tol == 1e-12 and p.newton_min_upd == 0
     rc, pop_b, aux_b = C.lbm39_query_bytes(p)
     assert rc == 0
     N = 480
-    Np = (N + 31) // 32 * 32
+    Np = (N + 63) // 64 * 64
     assert pop_b == 78 * 8 * Np
     assert aux_b >= 13 * 8 * Np
 
