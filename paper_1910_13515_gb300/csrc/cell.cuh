@@ -212,17 +212,18 @@ __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
 #pragma unroll
     for (int k = 0; k < NM; ++k) dl[k] = b[k];
     return ok;
+  } else {
+    float Ff[Q], J[NTRI], s[NM], bf[NM];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
+    gen::moments<float>(Ff, s, J);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) bf[k] = trunc_float(dl[k]);
+    const bool ok = ldlt_solve<float>(J, bf);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) dl[k] = exact_double(bf[k]);
+    return ok;
   }
-  float Ff[Q], J[NTRI], s[NM], bf[NM];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
-  gen::moments<float>(Ff, s, J);
-#pragma unroll
-  for (int k = 0; k < NM; ++k) bf[k] = trunc_float(dl[k]);
-  const bool ok = ldlt_solve<float>(J, bf);
-#pragma unroll
-  for (int k = 0; k < NM; ++k) dl[k] = exact_double(bf[k]);
-  return ok;
 }
 
 constexpr int LS_MAX = 30;
