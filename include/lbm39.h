@@ -178,6 +178,23 @@ int lbm39_load(lbm39_lattice* L, const void* buf);
  * cuda_stream as in lbm39_create.  Returns after enqueueing. */
 int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void* cuda_stream);
 
+/* Conserved sums (the conserved[] of lbm39_stats_t: mass, momentum x/y/z,
+ * total energy over the fluid cells) for callers that cannot allocate device
+ * memory -- for instance code that runs where cudaMalloc is unavailable or
+ * forbidden, or that must not grow the device footprint after start-up.  The
+ * paper has no counterpart: this is a service of the library.  Neither the
+ * caller nor the library allocates anything for it: the reduction's scratch
+ * is a fixed 320 KiB device array inside the library, present on every GPU
+ * that loads the library until the process exits.  The lattice is the input
+ * and sums5 (host, 5 float64) the output; the call waits for the lattice's
+ * stream.  The first call on a device looks up that array's device address
+ * (with the device current), so make it before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU race.  Lattices of more than
+ * 67,108,864 cells (8192 blocks of 8192 cells) are rejected with
+ * LBM39_ERR_ARG.  The block decomposition differs from lbm39_stats', so the
+ * sums agree with it to rounding, not bit for bit. */
+int lbm39_conserved_noalloc(lbm39_lattice* L, double* sums5);
+
 /* Releases the handle (not the caller's buffers).  NULL is a no-op. */
 void lbm39_destroy(lbm39_lattice* L);
 

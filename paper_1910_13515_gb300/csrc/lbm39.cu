@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -514,6 +515,105 @@ int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void*
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
   k_selftest_exp<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, y, ref, n);
   return last_launch();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Conserved sums for callers that cannot allocate device memory.
+//
+// The reduction's scratch (one partial per block, then the 5 results) is this
+// file-scope device array, 320 KiB held by every GPU that loads the library.
+// In host code its name is only a stand-in for the device object, so the
+// device address is looked up with cudaGetSymbolAddress once per device (on
+// the first call with that device current) and handed to the kernels.  Every
+// block writes its own partial before the final kernel reads it, so nothing
+// has to start at zero; calls that overlap on the GPU share the array and race.
+constexpr int NOALLOC_BLOCKS_MAX = 8192;
+constexpr int NOALLOC_THREADS = 128;
+constexpr long long NOALLOC_CELLS_PER_BLOCK = 8192;  // 64 cells per thread
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_BLOCKS_MAX * 5 + 8];
+
+// Sums over the fluid cells of block b's chunk [b*C, (b+1)*C) into partials[5b..5b+4].
+template <bool ODD, class P>
+__global__ void __launch_bounds__(NOALLOC_THREADS) k_conserved_chunks(Desc d, double* partials,
+                                                                      long long chunk) {
+  __shared__ double red[5][NOALLOC_THREADS];
+  double acc[5] = {0, 0, 0, 0, 0};
+  const long long c0 = (long long)blockIdx.x * chunk;
+  const long long c1 = std::min(d.N, c0 + chunk);
+  for (long long cell = c0 + threadIdx.x; cell < c1; cell += NOALLOC_THREADS) {
+    if (d.mask != nullptr && d.mask[cell] != MASK_FLUID) continue;
+    Nbr nb;
+    unsigned long long bits = 0;
+    if constexpr (ODD) {
+      nb = Nbr(d, coord_of(d, cell));
+      if (d.bounce) bits = d.bounce[cell];
+    }
+    const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+    acc[0] += r.rho;
+    acc[1] += r.jx;
+    acc[2] += r.jy;
+    acc[3] += r.jz;
+    acc[4] += 0.5 * r.e2;
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = NOALLOC_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+static double* noalloc_scratch(int* rc) {
+  static std::mutex mu;
+  static double* ptr[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    *rc = LBM39_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      *rc = LBM39_ERR_CUDA;
+      return nullptr;
+    }
+    ptr[dev] = static_cast<double*>(p);
+  }
+  *rc = LBM39_OK;
+  return ptr[dev];
+}
+
+extern "C" {
+
+int lbm39_conserved_noalloc(lbm39_lattice* L, double* sums5) {
+  if (!L || !sums5) return LBM39_ERR_ARG;
+  if (!L->initialized) return LBM39_ERR_STATE;
+  if (L->N > (long long)NOALLOC_BLOCKS_MAX * NOALLOC_CELLS_PER_BLOCK) return LBM39_ERR_ARG;
+  int rc = LBM39_OK;
+  double* scratch = noalloc_scratch(&rc);
+  if (!scratch) return rc;
+  const unsigned grid = (unsigned)((L->N + NOALLOC_CELLS_PER_BLOCK - 1) / NOALLOC_CELLS_PER_BLOCK);
+  double* results = scratch + NOALLOC_BLOCKS_MAX * 5;
+  const bool odd = L->t & 1;
+  if (L->mixed) {
+    if (odd) k_conserved_chunks<true, float><<<grid, NOALLOC_THREADS, 0, L->stream>>>(L->desc, scratch, NOALLOC_CELLS_PER_BLOCK);
+    else k_conserved_chunks<false, float><<<grid, NOALLOC_THREADS, 0, L->stream>>>(L->desc, scratch, NOALLOC_CELLS_PER_BLOCK);
+  } else {
+    if (odd) k_conserved_chunks<true, double><<<grid, NOALLOC_THREADS, 0, L->stream>>>(L->desc, scratch, NOALLOC_CELLS_PER_BLOCK);
+    else k_conserved_chunks<false, double><<<grid, NOALLOC_THREADS, 0, L->stream>>>(L->desc, scratch, NOALLOC_CELLS_PER_BLOCK);
+  }
+  k_sum_partials<<<1, 32, 0, L->stream>>>(scratch, (int)grid, results);
+  if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
+  CUDA_OK(cudaMemcpyAsync(sums5, results, sizeof(double) * 5, cudaMemcpyDeviceToHost, L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  return LBM39_OK;
 }
 
 void lbm39_destroy(lbm39_lattice* L) { delete L; }

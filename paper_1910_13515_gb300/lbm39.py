@@ -89,6 +89,7 @@ def _load():
         "lbm39_save": (i, [vp, vp]),
         "lbm39_load": (i, [vp, vp]),
         "lbm39_selftest_exp": (i, [vp, vp, vp, i64, vp]),
+        "lbm39_conserved_noalloc": (i, [vp, vp]),
         "lbm39_destroy": (None, [vp]),
         "lbm39_strerror": (ctypes.c_char_p, [i]),
     }
@@ -178,6 +179,10 @@ def lbm39_load(h, buf) -> int:
 
 def lbm39_selftest_exp(x, y, ref, n: int, stream) -> int:
     return _lib.lbm39_selftest_exp(x, y, ref, n, stream)
+
+
+def lbm39_conserved_noalloc(h, sums5_host) -> int:
+    return _lib.lbm39_conserved_noalloc(h, sums5_host)
 
 
 def lbm39_destroy(h) -> None:
