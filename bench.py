@@ -35,14 +35,41 @@ WORKLOADS = {
     "box128": "3-D periodic box 128^3 (profiling size), solenoidal velocity rms Ma=0.8, "
               "+-5% rho/T noise, seed 0, tau=0.55, alpha(eps) on",
     "sod": "Sod tube 400x1x1, outflow ends, tau=0.5 with alpha(eps)",
+    "serve": "serving form: Poisson stream of 64 seeded requests (Riemann tubes 200-4000 cells, "
+             "2-D shear layers 128^2-1024^2, 200-2000 steps), admitted into a 4 GiB budget",
 }
 
 # FP64 arithmetic of one fluid-cell update as executed by the step kernel, from ncu
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL): A + B * (Newton updates per cell)
 # + C * (extra equilibrium evaluations of the line search, per cell).  See profiles/.
-FP64_FLOPS_MODEL = {"fp64": (0.0, 0.0, 0.0), "mixed": (0.0, 0.0, 0.0)}
-FP64_PEAK_TFLOPS = 1.008   # measured DFMA throughput (own microbenchmark), profiles/
+FP64_FLOPS_MODEL = {"fp64": (1385.0, 2590.0), "mixed": (1314.0, 1015.0)}
+# DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
+# from ncu, per workload and precision, with the hash of the kernel sources they were
+# captured with; reported as null once the sources differ (profiles/ has the captures).
+NCU_TRAFFIC = {"kernel_hash": None, "gb_per_launch": {}}
+KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
+                  "lbm39.cu")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1910_13515_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 BYTES_PER_UPDATE = {"fp64": 78 * 8 * 2 + 13 * 8 * 2, "mixed": 78 * 4 * 2 + 13 * 8 * 2}
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure of the profiling recipe
+
+
+HBM_PEAK_GBS = _hbm_peak()
 
 
 def make_setup(name: str):
@@ -181,6 +208,73 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(elapsed_s: float, units: float, dist=None, device=None):
+    """Whole-job timing of weak-scaled replicas: the slowest rank's time and the units all
+    ranks processed (each rank runs its own lattice; no data-path collective)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed_s, units
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def run_serve(args, rank, world, local):
+    """Config 5: the serving form.  value = aggregate MLUPS over the whole stream (all cells x
+    steps of all requests / wall time from first arrival to last result); p50/p99 latency =
+    arrival to result read.  Baseline: a sample of the same requests run one after another
+    through plain lbm39_step (no packing)."""
+    import numpy as np
+    import torch
+
+    from paper_1910_13515_gb300 import inputs
+    from paper_1910_13515_gb300.lattice import Lattice
+    from paper_1910_13515_gb300.serve import GpuBackend, Scheduler
+
+    torch.cuda.set_device(local)
+    prec = 0 if args.precision == "fp64" else 1
+    reqs = inputs.serving_requests(64, seed=rank, rate_hz=args.serve_rate)
+    be = GpuBackend(precision=prec, max_lattices=64, max_cells=1 << 25,
+                    graph_steps=8, device=f"cuda:{local}")
+    warm = inputs.serving_requests(4, seed=1000 + rank, rate_hz=1e6, shear_sizes=(128,),
+                                   riemann_range=(200, 400), steps_range=(16, 24))
+    Scheduler(be, 4 << 30, 64, chunk_steps=64).run(warm)
+    with ClockSampler(local) as clk:
+        rep = Scheduler(be, 4 << 30, 64, chunk_steps=64).run(reqs)
+    clocks = clk.summary()
+    be.close()
+    sample = reqs[::4]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cs = 0
+    for r in sample:
+        L = Lattice.from_setup(r.setup, precision=prec, device=f"cuda:{local}")
+        L.step(r.setup.steps)
+        L.read_numpy()
+        cs += r.setup.ncells * r.setup.steps
+        L.close()
+    serial = cs / (time.perf_counter() - t0) / 1e6
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(rep.mlups, 3), "unit": "MLUPS",
+                "n_gpus": world, "steps": sum(r.setup.steps for r in reqs), "warmup": 4,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-storage/f64-solve",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS["serve"], "requests": len(reqs),
+                           "cell_steps": rep.cell_steps, "budget_gib": 4,
+                           "max_resident": rep.max_resident, "rounds": rep.rounds,
+                           "arrival_rate_hz": args.serve_rate},
+                "serving": {"p50_ms": round(rep.p50_ms, 2), "p99_ms": round(rep.p99_ms, 2),
+                            "aggregate_mlups": round(rep.mlups, 3),
+                            "serial_mlups": round(serial, 3),
+                            "speedup_vs_serial": round(rep.mlups / serial, 3),
+                            "serial_sample": f"{len(sample)} of the requests, one at a time"},
+                "clocks": clocks, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +286,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--serve-rate", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -202,6 +297,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world, local)
         return
 
     import numpy as np
@@ -243,29 +341,40 @@ def main():
         barrier()
     clocks = clk.summary()
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    elapsed_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([elapsed_ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_s, units = reduce_over_ranks(evs[0].elapsed_time(evs[-1]) * 1e-3,
+                                         float(N * args.steps), dist, f"cuda:{local}")
+    elapsed_ms = elapsed_s * 1e3
     if L.sync() != 0:
         raise RuntimeError("Newton failures in the timed region")
     st1 = L.stats()
     cell_steps = fluid * args.steps
     k_upd = (st1.newton_updates - st0.newton_updates) / cell_steps
-    value = N * args.steps * world / (elapsed_ms * 1e-3) / 1e6
+    value = units / elapsed_s / 1e6
 
     # dominant kernel (the fused step): per-launch duration on its own stream
     step_ms = float(np.mean(per_step))
-    A, B, Cc = FP64_FLOPS_MODEL[args.precision]
-    flops_cell = A + B * k_upd
-    achieved_tf = flops_cell * fluid / (step_ms * 1e-3) / 1e12 if flops_cell > 0 else None
+    scratch = torch.empty(1 << 21, dtype=torch.float64, device=f"cuda:{local}")
+    rc, peak_tf = C.lbm39_selftest_dfma(scratch.data_ptr(), scratch.numel() * 8,
+                                        stream.cuda_stream)
+    C.check(rc, "lbm39_selftest_dfma")
+    model = FP64_FLOPS_MODEL[args.precision]
+    achieved_tf = None
+    if model is not None:
+        achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
+    hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC["kernel_hash"] == kernel_source_hash():
+        traffic = NCU_TRAFFIC["gb_per_launch"].get(f"{args.workload}/{args.precision}")
     roofline = {"bound": "alu", "achieved": round(achieved_tf, 4) if achieved_tf else None,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4) if achieved_tf else None,
-                "traffic": None,
-                "peak_source": "measured DFMA throughput (of measured)",
-                "hbm_gbs": round(BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9, 1)}
+                "peak": round(peak_tf, 4), "unit": "TFLOP/s",
+                "frac": round(achieved_tf / peak_tf, 4) if achieved_tf else None,
+                "traffic": round(traffic * 1e9) if traffic else None,
+                "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
+                               "(of measured)",
+                "flops_per_cell_update": round(model[0] + model[1] * k_upd) if model else None,
+                "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": HBM_PEAK_GBS,
+                        "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),
+                        "bytes_per_update": BYTES_PER_UPDATE[args.precision]}}
 
     # end to end through the C ABI with host buffers: upload the initial fields from pinned
     # memory, then every step a step and a read-back of rho/u/T/p into pinned memory
@@ -283,12 +392,9 @@ def main():
             C.check(C.lbm39_step(L.h, 1))
             C.check(C.lbm39_read_host(L.h, h_out[0].data_ptr(), h_out[1].data_ptr(),
                                       h_out[4].data_ptr(), h_out[5].data_ptr()))
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device=f"cuda:{local}")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": round(N * ke * world / dt / 1e6, 3), "unit": "MLUPS",
+        dt, units_e2e = reduce_over_ranks(time.perf_counter() - t0, float(N * ke), dist,
+                                          f"cuda:{local}")
+        e2e = {"value": round(units_e2e / dt / 1e6, 3), "unit": "MLUPS",
                "h2d_bytes_per_step": int(5 * 8 * N / ke), "d2h_bytes_per_step": 6 * 8 * N,
                "steps": ke, "includes": "lbm39_init_host once (cold-start Newton) + per step "
                                        "lbm39_step(1) and lbm39_read_host of rho,u,T,p"}
@@ -318,6 +424,7 @@ def main():
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
             "gpu_launches": args.steps * (2 if L.has_ghosts else 1),
             "cpu_baseline": cpu,
+            "kernel_hash": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)
     L.close()

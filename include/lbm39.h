@@ -171,6 +171,46 @@ size_t lbm39_checkpoint_bytes(const lbm39_lattice* L);
 int lbm39_save(lbm39_lattice* L, void* buf);
 int lbm39_load(lbm39_lattice* L, const void* buf);
 
+/* ---- Serving form: packed steps of many resident lattices ----------------
+ * A batch advances up to max_lattices resident lattices (same precision,
+ * together at most max_cells cells) with one packed launch per time step: a
+ * launch's blocks are tiles of the lattices, each lattice at its own time
+ * (own AA parity) and stopping at its own end time, so every lattice gets
+ * exactly the arithmetic of lbm39_step.  Runs of graph_steps steps are
+ * captured once into a CUDA graph and replayed; the graph is re-captured
+ * after lbm39_batch_set.  The batch's device buffer (lbm39_batch_query_bytes)
+ * belongs to the caller, like every other buffer.  The caller orders the
+ * batch's stream after the lattices' streams (one shared stream does it). */
+typedef struct lbm39_batch lbm39_batch;
+
+int lbm39_batch_query_bytes(int32_t max_lattices, int64_t max_cells, size_t* bytes);
+
+/* precision: lbm39_precision of every lattice the batch will hold;
+ * graph_steps >= 1: steps per captured graph; buf: device, 256-byte aligned;
+ * cuda_stream: a created stream (NULL, the legacy stream, cannot be captured
+ * and is rejected with LBM39_ERR_ARG). */
+int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precision,
+                       int32_t graph_steps, void* buf, void* cuda_stream, lbm39_batch** out);
+
+/* Makes lattices[0..n) the resident set; lattice j steps until its time
+ * reaches t_end[j] (>= its current time).  Lattices must be initialised, of
+ * the batch's precision, and stay alive while resident.  Synchronous. */
+int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_t* t_end,
+                    int32_t n);
+
+/* Enqueues nsteps >= 0 packed steps on the batch's stream: each resident
+ * lattice advances min(nsteps, t_end - time) steps; lattice times (and so
+ * lbm39_read parities) are updated on return. */
+int lbm39_batch_run(lbm39_batch* B, int64_t nsteps);
+
+void lbm39_batch_destroy(lbm39_batch* B);
+
+/* Diagnostic: the GPU's FP64 FMA throughput (TFLOP/s, 2 flops per FMA) from a
+ * kernel of independent FMA chains on every SM, best of 3 launches timed with
+ * CUDA events on cuda_stream -- the ALU roofline of the FP64 step.  scratch:
+ * device buffer of at least 8 * 256 * 8 * (number of SMs) bytes.  Synchronous. */
+int lbm39_selftest_dfma(double* tflops, void* scratch, size_t scratch_bytes, void* cuda_stream);
+
 /* Diagnostic of the library's FP64 exponential (the table-driven method of
  * Tang, ACM TOMS 15(2) 1989, used for every f^eq evaluation): for n device
  * values x, writes y[i] = that exponential and ref[i] = CUDA's exp(x[i]), so a

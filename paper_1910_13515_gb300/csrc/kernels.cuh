@@ -252,6 +252,32 @@ __device__ __forceinline__ void flush_stats(unsigned int* s_ctr, unsigned long l
     if (s_ctr[k]) atomicAdd(ctr + k, (unsigned long long)s_ctr[k]);
 }
 
+// One fluid cell's time step (even or odd AA pass): phases A, B and C, with
+// the Newton statistics added to the block's counters.  w: the cell's workspace.
+template <bool ODD, class P, int BLK>
+__device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
+                                          unsigned int* s_ctr) {
+  WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
+  Nbr nb;
+  unsigned long long bits = 0;
+  if constexpr (ODD) {
+    nb = Nbr(d, coord_of(d, cell));
+    if (d.bounce) bits = d.bounce[cell];
+  }
+  const Macro M = gather_moments<ODD, P>(d, cell, nb, bits);
+  targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) lam[k] = d.lam[k * d.Np + cell];
+  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit);
+#pragma unroll
+  for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
+  const int branch = relax_push<ODD, P, BLK>(d, cell, nb, bits, M, F);
+  atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
+  atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
+  atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
+  atomicAdd(&s_ctr[CTR_EPS + branch], 1u);
+}
+
 // One time step over every fluid cell (even or odd AA pass).
 template <bool ODD, class P, int BLK>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
@@ -260,29 +286,8 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
   load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
-  const bool active = cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID);
-  if (active) {
-    WS<BLK> w{smem + threadIdx.x};
-    WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
-    Nbr nb;
-    unsigned long long bits = 0;
-    if constexpr (ODD) {
-      nb = Nbr(d, coord_of(d, cell));
-      if (d.bounce) bits = d.bounce[cell];
-    }
-    const Macro M = gather_moments<ODD, P>(d, cell, nb, bits);
-    targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = d.lam[k * d.Np + cell];
-    const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit);
-#pragma unroll
-    for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
-    const int branch = relax_push<ODD, P, BLK>(d, cell, nb, bits, M, F);
-    atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
-    atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
-    atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
-    atomicAdd(&s_ctr[CTR_EPS + branch], 1u);
-  }
+  if (cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID))
+    step_cell<ODD, P, BLK>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 
@@ -372,9 +377,7 @@ __global__ void k_bounce_bits(Desc d, unsigned long long* bounce) {
 // populations and outflow cells a copy of the cell with x clamped into
 // [3, nx-4], both in the reversed (post-collision) layout the odd pass reads.
 template <class P>
-__global__ void k_fill_even(Desc d) {
-  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= d.N) return;
+__device__ __forceinline__ void fill_even_cell(const Desc& d, long long cell) {
   const uint8_t mk = d.mask[cell];
   if (mk != MASK_FREE && mk != MASK_OUT) return;
   P* pop = static_cast<P*>(d.pop);
@@ -403,9 +406,8 @@ __global__ void k_fill_even(Desc d) {
 // post-collision population of the clamped cell c (which c pushed into
 // slot (c + xi_i, i), or bounced into (c, opp i) if c + xi_i is solid).
 template <class P>
-__global__ void k_fill_odd(Desc d) {
-  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= d.N || d.mask[cell] != MASK_FLUID) return;
+__device__ __forceinline__ void fill_odd_cell(const Desc& d, long long cell) {
+  if (d.mask[cell] != MASK_FLUID) return;
   const Coord c = coord_of(d, cell);
   const bool near = (!d.per[0] && (c.x < 6 || c.x >= d.nx - 6)) ||
                     (!d.per[1] && (c.y < 6 || c.y >= d.ny - 6)) ||
@@ -440,6 +442,18 @@ __global__ void k_fill_odd(Desc d) {
       pop[jg + cell] = pop[src + Q * d.Np];
     }
   }
+}
+
+template <class P>
+__global__ void k_fill_even(Desc d) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell < d.N) fill_even_cell<P>(d, cell);
+}
+
+template <class P>
+__global__ void k_fill_odd(Desc d) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell < d.N) fill_odd_cell<P>(d, cell);
 }
 
 // rho, u, T, p = rho T of cells [c0, c0 + len) into out arrays indexed by
@@ -501,6 +515,69 @@ __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
   if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// ---------------------------------------------------------------------------
+// Serving form: many resident lattices advanced by one packed launch per time
+// step.  A tile is one block of one lattice; each lattice keeps its own time
+// (and therefore its own AA parity) and stops at its own end time, so a packed
+// run gives every lattice exactly the arithmetic of stepping it alone.
+
+struct BatchEntry {
+  Desc d;
+  long long t0;     // the lattice's time at step index 0 of the current launch sequence
+  long long t_end;  // the lattice does not step past this time
+};
+
+struct Tile {
+  int lat;          // index into the batch entries
+  int pad;
+  long long cell0;  // first cell of the tile
+};
+
+template <class P, int BLK>
+__global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict__ E,
+                                                    const Tile* __restrict__ tiles, int s) {
+  extern __shared__ double smem[];
+  __shared__ unsigned int s_ctr[CTR_N];
+  __shared__ Desc sd;
+  __shared__ long long st;
+  const Tile tl = tiles[blockIdx.x];
+  if (threadIdx.x == 0) {
+    sd = E[tl.lat].d;
+    st = E[tl.lat].t0 + s < E[tl.lat].t_end ? E[tl.lat].t0 + s : -1;
+  }
+  for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
+  load_exp_table();  // also publishes sd and st
+  const long long t = st;
+  if (t < 0) return;  // this lattice has reached its end time (uniform over the block)
+  const long long cell = tl.cell0 + threadIdx.x;
+  if (cell < sd.N && (sd.mask == nullptr || sd.mask[cell] == MASK_FLUID)) {
+    WS<BLK> w{smem + threadIdx.x};
+    if (t & 1) step_cell<true, P, BLK>(sd, cell, w, s_ctr);
+    else step_cell<false, P, BLK>(sd, cell, w, s_ctr);
+  }
+  flush_stats<BLK>(s_ctr, sd.ctr);
+}
+
+// Boundary fills of the lattices that have freestream or outflow cells.
+template <class P>
+__global__ void k_batch_fill(const BatchEntry* __restrict__ E, const Tile* __restrict__ tiles,
+                             int s) {
+  const Tile tl = tiles[blockIdx.x];
+  const BatchEntry& e = E[tl.lat];
+  const long long t = e.t0 + s;
+  if (t >= e.t_end) return;
+  const long long cell = tl.cell0 + threadIdx.x;
+  if (cell >= e.d.N) return;
+  if (t & 1) fill_odd_cell<P>(e.d, cell);
+  else fill_even_cell<P>(e.d, cell);
+}
+
+// After a launch sequence of n steps: every lattice's t0 moves on by n.
+__global__ void k_batch_advance(BatchEntry* E, int nlat, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nlat) E[j].t0 += n;
+}
+
 // Library exponential and CUDA's exp side by side (diagnostic).
 __global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
   load_exp_table();
@@ -509,6 +586,20 @@ __global__ void k_selftest_exp(const double* x, double* y, double* ref, long lon
     y[i] = exp_tang(x[i]);
     ref[i] = exp(x[i]);
   }
+}
+
+// FP64 FMA throughput probe: 8 independent chains per thread (diagnostic).
+__global__ void k_selftest_dfma(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-9, x2 = x0 + 2e-9, x3 = x0 + 3e-9;
+  double x4 = x0 + 4e-9, x5 = x0 + 5e-9, x6 = x0 + 6e-9, x7 = x0 + 7e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
 __global__ void k_sum_partials(const double* partials, int nblocks, double* out5) {

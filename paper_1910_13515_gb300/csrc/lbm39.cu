@@ -509,12 +509,222 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   return LBM39_OK;
 }
 
+int lbm39_selftest_dfma(double* tflops, void* scratch, size_t scratch_bytes, void* cuda_stream) {
+  if (!tflops || !scratch) return LBM39_ERR_ARG;
+  int dev = 0, sms = 0;
+  CUDA_OK(cudaGetDevice(&dev));
+  CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8;
+  if (scratch_bytes < sizeof(double) * threads * (size_t)blocks) return LBM39_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t e0, e1;
+  CUDA_OK(cudaEventCreate(&e0));
+  CUDA_OK(cudaEventCreate(&e1));
+  const int iters = 2048;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    k_selftest_dfma<<<blocks, threads, 0, s>>>(static_cast<double*>(scratch), iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return LBM39_ERR_CUDA; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (last_launch() != LBM39_OK) return LBM39_ERR_CUDA;
+  const double fmas = (double)blocks * threads * iters * 32.0;
+  *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+  return LBM39_OK;
+}
+
 int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void* cuda_stream) {
   if (!x || !y || !ref || n < 0) return LBM39_ERR_ARG;
   if (n == 0) return LBM39_OK;
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
   k_selftest_exp<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, y, ref, n);
   return last_launch();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving form: packed steps of many lattices (see include/lbm39.h).
+
+struct lbm39_batch {
+  int maxlat = 0;
+  long long maxcells = 0, maxtiles = 0, maxftiles = 0;
+  int precision = LBM39_FP64;
+  int G = 1;
+  cudaStream_t stream = nullptr;
+  BatchEntry* dE = nullptr;
+  Tile* dT = nullptr;
+  Tile* dF = nullptr;
+  std::vector<BatchEntry> hE;
+  std::vector<Tile> hT, hF;
+  std::vector<lbm39_lattice*> lats;
+  std::vector<long long> tend;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;
+};
+
+namespace {
+struct BatchLayout {
+  size_t E, T, F, total;
+  long long maxtiles, maxftiles;
+};
+
+BatchLayout batch_layout(int maxlat, long long maxcells) {
+  BatchLayout b;
+  b.maxtiles = (maxcells + BLK - 1) / BLK + maxlat;
+  b.maxftiles = (maxcells + 255) / 256 + maxlat;
+  size_t off = 0;
+  b.E = off; off = align256(off + sizeof(BatchEntry) * maxlat);
+  b.T = off; off = align256(off + sizeof(Tile) * b.maxtiles);
+  b.F = off; off = align256(off + sizeof(Tile) * b.maxftiles);
+  b.total = off;
+  return b;
+}
+
+template <class P>
+int batch_enqueue(lbm39_batch* B, int s) {
+  const int nt = (int)B->hT.size(), nf = (int)B->hF.size();
+  if (nt) k_batch_step<P, BLK><<<nt, BLK, WS_BYTES, B->stream>>>(B->dE, B->dT, s);
+  if (nf) k_batch_fill<P><<<nf, 256, 0, B->stream>>>(B->dE, B->dF, s);
+  return last_launch();
+}
+
+int batch_steps(lbm39_batch* B, int n) {
+  for (int s = 0; s < n; ++s) {
+    const int rc = B->precision == LBM39_MIXED ? batch_enqueue<float>(B, s) : batch_enqueue<double>(B, s);
+    if (rc) return rc;
+  }
+  const int nl = (int)B->hE.size();
+  if (nl) k_batch_advance<<<(nl + 127) / 128, 128, 0, B->stream>>>(B->dE, nl, n);
+  return last_launch();
+}
+}  // namespace
+
+extern "C" {
+
+int lbm39_batch_query_bytes(int32_t max_lattices, int64_t max_cells, size_t* bytes) {
+  if (max_lattices < 1 || max_cells < 1 || !bytes) return LBM39_ERR_ARG;
+  *bytes = batch_layout(max_lattices, max_cells).total;
+  return LBM39_OK;
+}
+
+int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precision,
+                       int32_t graph_steps, void* buf, void* cuda_stream, lbm39_batch** out) {
+  if (!out) return LBM39_ERR_ARG;
+  *out = nullptr;
+  if (max_lattices < 1 || max_cells < 1 || graph_steps < 1 || !buf || ((uintptr_t)buf & 255))
+    return LBM39_ERR_ARG;
+  if (cuda_stream == nullptr) return LBM39_ERR_ARG;  // graphs cannot be captured on the legacy stream
+  if (precision != LBM39_FP64 && precision != LBM39_MIXED) return LBM39_ERR_ARG;
+  static bool attr = false;
+  if (!attr) {
+    CUDA_OK(cudaFuncSetAttribute(k_batch_step<double, BLK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_BYTES));
+    CUDA_OK(cudaFuncSetAttribute(k_batch_step<float, BLK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_BYTES));
+    attr = true;
+  }
+  lbm39_batch* B = new (std::nothrow) lbm39_batch;
+  if (!B) return LBM39_ERR_ARG;
+  const BatchLayout lay = batch_layout(max_lattices, max_cells);
+  char* b = static_cast<char*>(buf);
+  B->maxlat = max_lattices;
+  B->maxcells = max_cells;
+  B->maxtiles = lay.maxtiles;
+  B->maxftiles = lay.maxftiles;
+  B->precision = precision;
+  B->G = graph_steps;
+  B->stream = static_cast<cudaStream_t>(cuda_stream);
+  B->dE = reinterpret_cast<BatchEntry*>(b + lay.E);
+  B->dT = reinterpret_cast<Tile*>(b + lay.T);
+  B->dF = reinterpret_cast<Tile*>(b + lay.F);
+  *out = B;
+  return LBM39_OK;
+}
+
+int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_t* t_end,
+                    int32_t n) {
+  if (!B || n < 0 || n > B->maxlat || (n > 0 && (!lattices || !t_end))) return LBM39_ERR_ARG;
+  long long cells = 0;
+  for (int j = 0; j < n; ++j) {
+    lbm39_lattice* L = lattices[j];
+    if (!L) return LBM39_ERR_ARG;
+    if (!L->initialized) return LBM39_ERR_STATE;
+    if (L->p.precision != B->precision || t_end[j] < L->t) return LBM39_ERR_ARG;
+    cells += L->N;
+  }
+  if (cells > B->maxcells) return LBM39_ERR_ARG;
+  B->hE.clear(); B->hT.clear(); B->hF.clear(); B->lats.clear(); B->tend.clear();
+  for (int j = 0; j < n; ++j) {
+    lbm39_lattice* L = lattices[j];
+    BatchEntry e;
+    e.d = L->desc;
+    e.t0 = L->t;
+    e.t_end = t_end[j];
+    B->hE.push_back(e);
+    B->lats.push_back(L);
+    B->tend.push_back(t_end[j]);
+    for (long long c = 0; c < L->N; c += BLK) B->hT.push_back(Tile{j, 0, c});
+    if (L->ghosts)
+      for (long long c = 0; c < L->N; c += 256) B->hF.push_back(Tile{j, 0, c});
+  }
+  if ((long long)B->hT.size() > B->maxtiles || (long long)B->hF.size() > B->maxftiles)
+    return LBM39_ERR_ARG;
+  if (n) {
+    CUDA_OK(cudaMemcpyAsync(B->dE, B->hE.data(), sizeof(BatchEntry) * n, cudaMemcpyHostToDevice, B->stream));
+    CUDA_OK(cudaMemcpyAsync(B->dT, B->hT.data(), sizeof(Tile) * B->hT.size(), cudaMemcpyHostToDevice, B->stream));
+    if (!B->hF.empty())
+      CUDA_OK(cudaMemcpyAsync(B->dF, B->hF.data(), sizeof(Tile) * B->hF.size(), cudaMemcpyHostToDevice, B->stream));
+  }
+  CUDA_OK(cudaStreamSynchronize(B->stream));
+  B->dirty = true;
+  return LBM39_OK;
+}
+
+int lbm39_batch_run(lbm39_batch* B, int64_t nsteps) {
+  if (!B || nsteps < 0) return LBM39_ERR_ARG;
+  if (B->hE.empty() || nsteps == 0) return LBM39_OK;
+  int64_t done = 0;
+  while (nsteps - done >= B->G) {
+    if (B->dirty || !B->exec) {
+      if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+      cudaGraph_t g = nullptr;
+      CUDA_OK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = batch_steps(B, B->G);
+      const cudaError_t ec = cudaStreamEndCapture(B->stream, &g);
+      if (rc != LBM39_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return LBM39_ERR_CUDA;
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&B->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) { B->exec = nullptr; return LBM39_ERR_CUDA; }
+      B->dirty = false;
+    }
+    CUDA_OK(cudaGraphLaunch(B->exec, B->stream));
+    done += B->G;
+  }
+  if (nsteps > done) {
+    const int rc = batch_steps(B, (int)(nsteps - done));
+    if (rc) return rc;
+  }
+  for (size_t j = 0; j < B->lats.size(); ++j) {
+    B->lats[j]->t = std::min<long long>(B->lats[j]->t + nsteps, B->tend[j]);
+    B->hE[j].t0 += nsteps;
+  }
+  return LBM39_OK;
+}
+
+void lbm39_batch_destroy(lbm39_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  delete B;
 }
 
 }  // extern "C"

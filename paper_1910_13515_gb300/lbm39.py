@@ -89,7 +89,14 @@ def _load():
         "lbm39_save": (i, [vp, vp]),
         "lbm39_load": (i, [vp, vp]),
         "lbm39_selftest_exp": (i, [vp, vp, vp, i64, vp]),
+        "lbm39_selftest_dfma": (i, [ctypes.POINTER(ctypes.c_double), vp, sz, vp]),
         "lbm39_conserved_noalloc": (i, [vp, vp]),
+        "lbm39_batch_query_bytes": (i, [ctypes.c_int32, i64, ctypes.POINTER(sz)]),
+        "lbm39_batch_create": (i, [ctypes.c_int32, i64, ctypes.c_int32, ctypes.c_int32, vp, vp,
+                                   ctypes.POINTER(vp)]),
+        "lbm39_batch_set": (i, [vp, vp, vp, ctypes.c_int32]),
+        "lbm39_batch_run": (i, [vp, i64]),
+        "lbm39_batch_destroy": (None, [vp]),
         "lbm39_destroy": (None, [vp]),
         "lbm39_strerror": (ctypes.c_char_p, [i]),
     }
@@ -177,12 +184,49 @@ def lbm39_load(h, buf) -> int:
     return _lib.lbm39_load(h, buf)
 
 
+def lbm39_selftest_dfma(scratch, nbytes: int, stream):
+    """Returns (rc, TFLOP/s)."""
+    t = ctypes.c_double()
+    rc = _lib.lbm39_selftest_dfma(ctypes.byref(t), scratch, nbytes, stream)
+    return rc, t.value
+
+
 def lbm39_selftest_exp(x, y, ref, n: int, stream) -> int:
     return _lib.lbm39_selftest_exp(x, y, ref, n, stream)
 
 
 def lbm39_conserved_noalloc(h, sums5_host) -> int:
     return _lib.lbm39_conserved_noalloc(h, sums5_host)
+
+
+def lbm39_batch_query_bytes(max_lattices: int, max_cells: int):
+    b = ctypes.c_size_t()
+    rc = _lib.lbm39_batch_query_bytes(max_lattices, max_cells, ctypes.byref(b))
+    return rc, b.value
+
+
+def lbm39_batch_create(max_lattices, max_cells, precision, graph_steps, buf, stream):
+    """Returns (rc, handle)."""
+    h = ctypes.c_void_p()
+    rc = _lib.lbm39_batch_create(max_lattices, max_cells, precision, graph_steps, buf, stream,
+                                 ctypes.byref(h))
+    return rc, h.value
+
+
+def lbm39_batch_set(b, handles, t_end) -> int:
+    n = len(handles)
+    arr = (ctypes.c_void_p * max(n, 1))(*handles)
+    te = (ctypes.c_int64 * max(n, 1))(*[int(t) for t in t_end])
+    return _lib.lbm39_batch_set(b, ctypes.cast(arr, ctypes.c_void_p),
+                                ctypes.cast(te, ctypes.c_void_p), n)
+
+
+def lbm39_batch_run(b, nsteps: int) -> int:
+    return _lib.lbm39_batch_run(b, nsteps)
+
+
+def lbm39_batch_destroy(b) -> None:
+    _lib.lbm39_batch_destroy(b)
 
 
 def lbm39_destroy(h) -> None:

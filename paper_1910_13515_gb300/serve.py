@@ -1,0 +1,183 @@
+"""Serving form: continuous batching of many lattice simulations on one GPU.
+
+Requests (a Setup and a number of steps) arrive on a clock.  The scheduler
+admits waiting requests whenever a slot and enough of the device-memory budget
+are free, keeps admitted lattices resident, and advances all of them together
+through lbm39_batch_run (one packed launch per time step, runs of graph_steps
+steps replayed from a captured CUDA graph).  A lattice that reaches its step
+count is read out and freed, which frees memory for the next requests, so work
+that arrives while others run overlaps with them on the device.
+
+Scheduler holds the policy and is independent of the GPU (a test drives it with a
+fake backend); GpuBackend does the device work through the C ABI.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .inputs import Request
+
+
+@dataclass
+class Job:
+    req: Request
+    bytes: int
+    steps: int
+    handle: object = None          # backend's lattice
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    result: tuple = None
+    done_steps: int = 0
+
+
+@dataclass
+class Report:
+    latencies_s: list
+    wall_s: float
+    cell_steps: int
+    results: dict = field(default_factory=dict)
+    max_resident: int = 0
+    rounds: int = 0
+
+    @property
+    def p50_ms(self) -> float:
+        return float(np.percentile(self.latencies_s, 50) * 1e3)
+
+    @property
+    def p99_ms(self) -> float:
+        return float(np.percentile(self.latencies_s, 99) * 1e3)
+
+    @property
+    def mlups(self) -> float:
+        return self.cell_steps / self.wall_s / 1e6
+
+
+class Scheduler:
+    """Admission by memory budget and slots; run lengths bounded by the soonest finishing
+    resident job and by `chunk_steps` (so new arrivals wait at most one chunk)."""
+
+    def __init__(self, backend, budget_bytes: int, max_resident: int, chunk_steps: int = 64,
+                 clock=time.perf_counter, sleep=time.sleep):
+        self.be = backend
+        self.budget = budget_bytes
+        self.max_resident = max_resident
+        self.chunk = chunk_steps
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests) -> Report:
+        pending = deque(sorted(requests, key=lambda r: r.arrival_s))
+        for r in pending:
+            if self.be.bytes_for(r.setup) > self.budget:
+                raise ValueError(f"request {r.rid} needs more than the whole memory budget")
+        waiting: deque = deque()
+        active: list = []
+        done: dict = {}
+        used = 0
+        t0 = self.clock()
+        max_res = 0
+        rounds = 0
+        while pending or waiting or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival_s <= now:
+                r = pending.popleft()
+                waiting.append(Job(r, self.be.bytes_for(r.setup), r.setup.steps))
+            admitted = False
+            while waiting and len(active) < self.max_resident and \
+                    used + waiting[0].bytes <= self.budget:
+                j = waiting.popleft()
+                j.handle = self.be.admit(j.req.setup)
+                j.t_admit = self.clock() - t0
+                used += j.bytes
+                active.append(j)
+                admitted = True
+            max_res = max(max_res, len(active))
+            if not active:
+                if pending:  # idle until the next arrival
+                    self.sleep(max(0.0, pending[0].arrival_s - (self.clock() - t0)))
+                continue
+            if admitted or self.be.needs_set:
+                self.be.set_resident([j.handle for j in active], [j.steps for j in active])
+            n = min(self.chunk, min(j.steps - j.done_steps for j in active))
+            self.be.run(n)
+            rounds += 1
+            for j in active:
+                j.done_steps += n
+            finished = [j for j in active if j.done_steps >= j.steps]
+            if finished:
+                for j in finished:
+                    j.result = self.be.read(j.handle)
+                    j.t_done = self.clock() - t0
+                    self.be.release(j.handle)
+                    used -= j.bytes
+                    done[j.req.rid] = j
+                active = [j for j in active if j.done_steps < j.steps]
+                self.be.needs_set = True
+        wall = max(j.t_done for j in done.values()) - min(j.req.arrival_s for j in done.values())
+        lat = [j.t_done - j.req.arrival_s for j in done.values()]
+        cells = sum(j.req.setup.ncells * j.steps for j in done.values())
+        return Report(lat, wall, cells, {rid: j.result for rid, j in done.items()}, max_res,
+                      rounds)
+
+
+class GpuBackend:
+    """Lattices on one GPU, advanced together by a batch of the C ABI."""
+
+    def __init__(self, precision=0, max_lattices: int = 64, max_cells: int = 1 << 25,
+                 graph_steps: int = 8, device="cuda"):
+        import torch
+
+        from . import lbm39 as C
+        self.torch, self.C = torch, C
+        self.device = torch.device(device)
+        # graph capture needs a created stream (not the legacy default stream)
+        self.stream = torch.cuda.Stream(self.device)
+        self.precision = precision
+        rc, nbytes = C.lbm39_batch_query_bytes(max_lattices, max_cells)
+        C.check(rc, "lbm39_batch_query_bytes")
+        self.buf = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=self.device)
+        rc, self.b = C.lbm39_batch_create(max_lattices, max_cells, precision, graph_steps,
+                                          self.buf.data_ptr(), self.stream.cuda_stream)
+        C.check(rc, "lbm39_batch_create")
+        self.needs_set = True
+
+    def bytes_for(self, setup) -> int:
+        from .lattice import params_from_setup
+        rc, pop, aux = self.C.lbm39_query_bytes(params_from_setup(setup, self.precision))
+        self.C.check(rc, "lbm39_query_bytes")
+        return pop + aux + setup.ncells
+
+    def admit(self, setup):
+        from .lattice import Lattice
+        L = Lattice.from_setup(setup, precision=self.precision, device=self.device,
+                               stream=self.stream)
+        return L
+
+    def set_resident(self, lattices, steps):
+        # every lattice starts at time 0, so its end time is its step count
+        self.C.check(self.C.lbm39_batch_set(self.b, [L.h for L in lattices], list(steps)),
+                     "lbm39_batch_set")
+        self.needs_set = False
+
+    def run(self, n: int):
+        self.C.check(self.C.lbm39_batch_run(self.b, n), "lbm39_batch_run")
+        self.stream.synchronize()
+
+    def read(self, L):
+        failed = L.sync()
+        if failed:
+            raise RuntimeError(f"{failed} Newton failures in a served lattice")
+        return L.read_numpy()
+
+    def release(self, L):
+        L.close()
+        L.pop = L.aux = L.mask = None
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.C.lbm39_batch_destroy(self.b)
+            self.b = None

@@ -1,0 +1,44 @@
+"""The N > 1 path of bench.py (replicas, weak scaling) on CPU: two gloo ranks, max-over-ranks
+time and summed units, as the driver's torchrun launch would produce."""
+import os
+import socket
+import sys
+
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, u = bench.reduce_over_ranks(1.0 + rank, 100.0 * (rank + 1), dist, "cpu")
+    out[rank] = (t, u)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_reduction_max_time_sum_units():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+    assert out[0] == (2.0, 300.0) and out[1] == (2.0, 300.0)
+
+
+def test_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_over_ranks(1.5, 10.0, None) == (1.5, 10.0)

@@ -1,0 +1,106 @@
+"""Host-side logic of the serving scheduler (no GPU): admission by memory budget and slots,
+exact step counts, latency accounting."""
+import numpy as np
+
+from paper_1910_13515_gb300 import inputs
+from paper_1910_13515_gb300.serve import Scheduler
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeBackend:
+    """Each run of n steps costs n * cells * 1e-6 s of fake time."""
+
+    def __init__(self, clock):
+        self.clock = clock
+        self.needs_set = True
+        self.resident = []
+        self.steps_done = {}
+        self.max_bytes_seen = 0
+        self.live = {}
+
+    def bytes_for(self, setup):
+        return setup.ncells * 100
+
+    def admit(self, setup):
+        h = object()
+        self.live[h] = setup
+        self.steps_done[h] = 0
+        self.max_bytes_seen = max(self.max_bytes_seen,
+                                  sum(self.bytes_for(s) for s in self.live.values()))
+        return h
+
+    def set_resident(self, handles, steps):
+        self.resident = list(zip(handles, steps))
+        self.needs_set = False
+
+    def run(self, n):
+        cells = 0
+        for h, target in self.resident:
+            k = min(n, target - self.steps_done[h])
+            self.steps_done[h] += k
+            cells += self.live[h].ncells * k
+        self.clock.t += cells * 1e-6 + 1e-6
+
+    def read(self, h):
+        return self.steps_done[h]
+
+    def release(self, h):
+        del self.live[h]
+
+
+def make_requests(n=12, seed=4):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for rid in range(n):
+        t += rng.exponential(0.01)
+        L = int(rng.choice([8, 16, 32]))
+        s = inputs.shear_layer(L, 1.0, steps=int(rng.integers(5, 40)))
+        reqs.append(inputs.Request(rid, t, s))
+    return reqs
+
+
+def test_every_request_gets_exactly_its_steps_within_budget():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = make_requests()
+    budget = 3 * 32 * 32 * 100
+    rep = Scheduler(be, budget, max_resident=4, chunk_steps=7, clock=clock,
+                    sleep=clock.sleep).run(reqs)
+    assert sorted(rep.results) == [r.rid for r in reqs]
+    for r in reqs:
+        assert rep.results[r.rid] == r.setup.steps
+    assert be.max_bytes_seen <= budget
+    assert 1 <= rep.max_resident <= 4
+    assert all(lat > 0 for lat in rep.latencies_s)
+    assert rep.cell_steps == sum(r.setup.ncells * r.setup.steps for r in reqs)
+
+
+def test_requests_overlap_when_budget_allows():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = make_requests(8, seed=1)
+    rep = Scheduler(be, 10 ** 12, max_resident=64, chunk_steps=1000, clock=clock,
+                    sleep=clock.sleep).run(reqs)
+    assert rep.max_resident >= 2
+
+
+def test_oversized_request_is_rejected():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = make_requests(2)
+    try:
+        Scheduler(be, 10, max_resident=2, clock=clock, sleep=clock.sleep).run(reqs)
+    except ValueError:
+        return
+    raise AssertionError("expected ValueError")
