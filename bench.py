@@ -46,7 +46,10 @@ FP64_FLOPS_MODEL = {"fp64": (1385.0, 2590.0), "mixed": (1314.0, 1015.0)}
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the kernel sources they were
 # captured with; reported as null once the sources differ (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": None, "gb_per_launch": {}}
+NCU_TRAFFIC = {"kernel_hash": "c21a815387c50587",
+               "gb_per_launch": {"naca/fp64": 3.473, "naca/mixed": 1.722,
+                                 "box256/fp64": 35.76, "box256/mixed": 13.74,
+                                 "box128/fp64": 4.470, "box128/mixed": 1.717}}
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                   "lbm39.cu")
 
@@ -286,7 +289,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
-    ap.add_argument("--serve-rate", type=float, default=3.0)
+    ap.add_argument("--serve-rate", type=float, default=0.8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
