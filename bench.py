@@ -61,7 +61,8 @@ def kernel_source_hash() -> str:
         with open(os.path.join(ROOT, "paper_1910_13515_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-BYTES_PER_UPDATE = {"fp64": 78 * 8 * 2 + 13 * 8 * 2, "mixed": 78 * 4 * 2 + 13 * 8 * 2}
+# populations read + written, and the per-cell solver state (lam and F: 52 FP64) read + written
+BYTES_PER_UPDATE = {"fp64": 78 * 8 * 2 + 52 * 8 * 2, "mixed": 78 * 4 * 2 + 52 * 8 * 2}
 
 
 def _hbm_peak():
@@ -75,19 +76,26 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 
 
-def make_setup(name: str):
+def make_setup(name: str, mach: float = 0.8):
     from paper_1910_13515_gb300 import inputs
     if name == "naca":
         return inputs.naca()
     if name == "box256":
-        return inputs.box(n=256, seed=0)
+        return inputs.box(n=256, seed=0, mach_rms=mach)
     if name == "box384":
-        return inputs.box(n=384, seed=0)
+        return inputs.box(n=384, seed=0, mach_rms=mach)
     if name == "box128":
-        return inputs.box(n=128, seed=0)
+        return inputs.box(n=128, seed=0, mach_rms=mach)
     if name == "sod":
         return inputs.sod(400)
     raise ValueError(name)
+
+
+def workload_text(args) -> str:
+    text = WORKLOADS[args.workload]
+    if args.workload.startswith("box") and args.mach != 0.8:
+        text = text.replace("rms Ma=0.8", f"rms Ma={args.mach:g}")
+    return text
 
 
 def crop_setup(s, name: str):
@@ -186,7 +194,7 @@ def run_reference(args, rank, world):
     bounded sample (a window) of the same workload."""
     if rank != 0:
         return
-    s = make_setup(args.workload)
+    s = make_setup(args.workload, args.mach)
     c, desc = crop_setup(s, args.workload)
     from oracle import oracle39 as o
     cfg = o.Config(nx=c.nx, ny=c.ny, nz=c.nz, periodic=c.periodic, gamma=c.gamma, tau=c.tau,
@@ -202,7 +210,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload] + f" [oracle on a {desc}]",
+            "config": {"workload": workload_text(args) + f" [oracle on a {desc}]",
                        "cells": c.ncells},
             "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": threads,
                              "kind": "oracle", "sample": desc},
@@ -290,6 +298,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--serve-rate", type=float, default=0.8)
+    ap.add_argument("--mach", type=float, default=0.8,
+                    help="box workloads: rms Mach number of the initial velocity field")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="precision form: also run the FP64 path and report L1 error, drift, speedup")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -321,11 +333,12 @@ def main():
     from paper_1910_13515_gb300.lattice import Lattice
 
     prec = C.LBM39_FP64 if args.precision == "fp64" else C.LBM39_MIXED
-    s = make_setup(args.workload)
+    s = make_setup(args.workload, args.mach)
     L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}")
     stream = L.stream
     N = s.ncells
-    fluid = L.stats().fluid_cells
+    st_init = L.stats()
+    fluid = st_init.fluid_cells
 
     L.step(args.warmup)
     if L.sync() != 0:
@@ -366,7 +379,7 @@ def main():
         achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
     hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["kernel_hash"] == kernel_source_hash():
+    if NCU_TRAFFIC["kernel_hash"] == kernel_source_hash() and args.mach == 0.8:
         traffic = NCU_TRAFFIC["gb_per_launch"].get(f"{args.workload}/{args.precision}")
     roofline = {"bound": "alu", "achieved": round(achieved_tf, 4) if achieved_tf else None,
                 "peak": round(peak_tf, 4), "unit": "TFLOP/s",
@@ -402,6 +415,40 @@ def main():
                "steps": ke, "includes": "lbm39_init_host once (cold-start Newton) + per step "
                                        "lbm39_step(1) and lbm39_read_host of rho,u,T,p"}
 
+    # precision form against the FP64 path on the same input and step count
+    form = None
+    if args.compare_fp64 and prec == C.LBM39_MIXED:
+        mixed_state = L.read_numpy()
+        st_end = L.stats()
+        Lf = Lattice.from_setup(s, precision=C.LBM39_FP64, device=f"cuda:{local}")
+        Lf.step(args.warmup)
+        ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ef0.record(Lf.stream)
+        Lf.step(args.steps)
+        ef1.record(Lf.stream)
+        if Lf.sync() != 0:
+            raise RuntimeError("Newton failures in the FP64 comparison run")
+        fp64_state = Lf.read_numpy()
+        fp64_mlups = N * args.steps / (ef0.elapsed_time(ef1) * 1e-3) / 1e6
+        Lf.close()
+        fl = s.mask == 0
+        (rm, um, Tm, _), (rf, uf, Tf, _) = mixed_state, fp64_state
+        l1 = [float(np.abs(rm[fl] - rf[fl]).mean() / np.abs(rf[fl]).mean()),
+              float(np.abs(um[:, fl] - uf[:, fl]).mean() / np.sqrt((uf[:, fl] ** 2).sum(0)).mean()),
+              float(np.abs(Tm[fl] - Tf[fl]).mean() / np.abs(Tf[fl]).mean())]
+        c0, c1 = np.array(st_init.conserved), np.array(st_end.conserved)
+        nsteps = args.warmup + args.steps
+        drift = (np.abs(c1 - c0) / np.array([c0[0]] * 4 + [c0[4]])).tolist()
+        form = {"compared_after_steps": nsteps,
+                "l1_rel_vs_fp64_rho_u_T": [float("%.3e" % v) for v in l1],
+                "conservation_drift_rel_mass_mom_xyz_energy": [float("%.3e" % v) for v in drift],
+                "conservation_drift_per_1000_steps": [float("%.3e" % (v * 1000 / nsteps))
+                                                      for v in drift],
+                "fp64_mlups_same_run": round(fp64_mlups, 3),
+                "speedup_vs_fp64": round(value / fp64_mlups, 3),
+                "note": "FP64 path parity-checked against the FP64 oracle; mass and momentum "
+                        "drift relative to the total mass"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c, desc = crop_setup(s, args.workload)
@@ -417,7 +464,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32-storage/f64-solve",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "precision": args.precision,
+            "config": {"workload": workload_text(args), "precision": args.precision,
                        "cells": N, "fluid_cells": int(fluid),
                        "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
                        "newton_updates_per_cell": round(k_upd, 4),
@@ -427,6 +474,7 @@ def main():
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
             "gpu_launches": args.steps * (2 if L.has_ghosts else 1),
             "cpu_baseline": cpu,
+            "precision_form": form,
             "kernel_hash": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

@@ -111,9 +111,10 @@ void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
 int lbm39_velocities(int32_t* vel, double* w);
 
 /* Sizes in bytes of the two device buffers a lattice needs: the populations
- * (39 f and 39 g planes, FP64 or FP32) and the auxiliary buffer (multipliers
- * carried between steps for the warm start, counters, reduction scratch and
- * host staging).  Both buffers must be 256-byte aligned. */
+ * (39 f and 39 g planes, FP64 or FP32) and the auxiliary buffer (the per-cell
+ * solver state carried between steps for the warm start -- the 13 multipliers
+ * and the 39 normalised equilibrium values they give, 52 FP64 planes -- counters,
+ * reduction scratch and host staging).  Both buffers must be 256-byte aligned. */
 int lbm39_query_bytes(const lbm39_params* p, size_t* pop_bytes, size_t* aux_bytes);
 
 /* Creates a lattice over caller-owned device buffers.  vel/w (host) must equal
@@ -162,7 +163,7 @@ int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double*
 /* Waits for the stream and fills *s (counters and conserved sums). */
 int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s);
 
-/* Bytes of a checkpoint (populations, multipliers, time and parity). */
+/* Bytes of a checkpoint (populations, per-cell solver state, time and parity). */
 size_t lbm39_checkpoint_bytes(const lbm39_lattice* L);
 
 /* Copies the full state into / from a caller buffer of

@@ -93,30 +93,35 @@ __device__ __noinline__ void exp_all_slow(double* Fp) {
 
 // F_i = exp(sum_k lam_k phi_k(xi_i)) (Eq. discrete-equilibrium / rho) into F,
 // and the constraint residual G_k = sum_i F_i phi_k(xi_i) - m_k (Eq. constraints).
+// from_F: F already holds exp(Phi lam) (kept from the previous step), so only
+// the moments are formed -- the same numbers, bit for bit, as evaluating again.
 template <int BLK>
 __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> F, WS<BLK> m,
-                                                 double (&G)[NM]) {
+                                                 double (&G)[NM], bool from_F) {
   double x[Q];
-  {
+  if (from_F) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) x[i] = F[i];
+  } else {
     double l[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) l[k] = lam[k];
     gen::exponents(l, x);
-  }
-  int wide = 0;
+    int wide = 0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
-  if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
+    for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
+    if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
 #pragma unroll
-    for (int i = 0; i < Q; ++i) F[i] = x[i];
-    exp_all_slow<BLK>(F.p);
+      for (int i = 0; i < Q; ++i) F[i] = x[i];
+      exp_all_slow<BLK>(F.p);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) x[i] = F[i];
-  } else {
+      for (int i = 0; i < Q; ++i) x[i] = F[i];
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      x[i] = exp_tang_core(x[i]);
-      F[i] = x[i];
+      for (int i = 0; i < Q; ++i) {
+        x[i] = exp_tang_core(x[i]);
+        F[i] = x[i];
+      }
     }
   }
   double s[NM];
@@ -241,8 +246,11 @@ struct NewtonResult {
 // decreases.  On return F holds exp(Phi lam) at the returned lam.
 // One evaluation site and one direction site keep the unrolled code small;
 // trial point and direction live in the workspace (w: the cell's workspace).
+// cached: F already holds exp(Phi lam) for the starting lam (the previous
+// step's last evaluation, kept per cell), so the first evaluation skips the
+// exponentials.
 template <int BLK, bool MIXED>
-__device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit) {
+__device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached) {
   WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), lt = w.at(WS_LT),
           dl = w.at(WS_DL);
 #pragma unroll
@@ -252,7 +260,7 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit) {
   double t = 0.0, s0 = 0.0;
   for (;;) {
     double G[NM];
-    eval_equilibrium<BLK>(lt, F, m, G);
+    eval_equilibrium<BLK>(lt, F, m, G, first && cached);
     if (restore) break;  // F is back at the last accepted lam after a failed line search
     if (!first && !polished && !(sum_sq(G) < s0)) {  // reject: halve the step
       if (++ls > LS_MAX) {

@@ -29,7 +29,8 @@ namespace lbm39 {
 
 struct Desc {
   void* pop;                          // 78 planes of P
-  double* lam;                        // 13 planes, multipliers kept between steps
+  double* lam;                        // 13 planes of multipliers kept between steps, then
+                                      // 39 planes of F_i = exp(Phi lam) at them
   const uint8_t* mask;                // nullptr: every cell fluid, all axes periodic
   const unsigned long long* bounce;   // bit i: the source x - xi_i is solid (nullptr: none)
   unsigned long long* ctr;            // counters (CTR_*)
@@ -252,6 +253,28 @@ __device__ __forceinline__ void flush_stats(unsigned int* s_ctr, unsigned long l
     if (s_ctr[k]) atomicAdd(ctr + k, (unsigned long long)s_ctr[k]);
 }
 
+// Per-cell solver state between steps: lam (13 planes) and F = exp(Phi lam)
+// (39 planes), in that order from Desc::lam.
+constexpr int SOLVER_PLANES = NM + Q;
+
+template <int BLK>
+__device__ __forceinline__ void load_solver_state(const Desc& d, long long cell, WS<BLK> w) {
+  const double* __restrict__ st = d.lam;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) w[WS_LAM + k] = st[k * d.Np + cell];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) w[WS_E + i] = st[(NM + i) * d.Np + cell];
+}
+
+template <int BLK>
+__device__ __forceinline__ void store_solver_state(const Desc& d, long long cell, WS<BLK> w) {
+  double* __restrict__ st = d.lam;
+#pragma unroll
+  for (int k = 0; k < NM; ++k) st[k * d.Np + cell] = w[WS_LAM + k];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) st[(NM + i) * d.Np + cell] = w[WS_E + i];
+}
+
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 template <bool ODD, class P, int BLK>
@@ -266,11 +289,9 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   }
   const Macro M = gather_moments<ODD, P>(d, cell, nb, bits);
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
-#pragma unroll
-  for (int k = 0; k < NM; ++k) lam[k] = d.lam[k * d.Np + cell];
-  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit);
-#pragma unroll
-  for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
+  load_solver_state<BLK>(d, cell, w);
+  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit, true);
+  store_solver_state<BLK>(d, cell, w);
   const int branch = relax_push<ODD, P, BLK>(d, cell, nb, bits, M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
@@ -320,18 +341,17 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
       WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
       targets<BLK>(ux, uy, uz, TT, m);
       gaussian_guess<BLK>(ux, uy, uz, TT, lam);
-      const NewtonResult nr = newton<BLK, false>(w, d.ph, maxit);
+      const NewtonResult nr = newton<BLK, false>(w, d.ph, maxit, false);
       const double cgr = d.ph.cg * TT * rr;
       for (int i = 0; i < Q; ++i) {
         pop[(long long)i * d.Np + cell] = to_store<P>(d, i, rr * F[i]);
         pop[(long long)(Q + i) * d.Np + cell] = to_store<P>(d, Q + i, cgr * F[i]);
       }
-#pragma unroll
-      for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = lam[k];
+      store_solver_state<BLK>(d, cell, w);
       atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
     } else {
       for (int j = 0; j < 2 * Q; ++j) pop[(long long)j * d.Np + cell] = P(0);
-      for (int k = 0; k < NM; ++k) d.lam[k * d.Np + cell] = 0.0;
+      for (int k = 0; k < SOLVER_PLANES; ++k) d.lam[k * d.Np + cell] = 0.0;
     }
   }
   flush_stats<BLK>(s_ctr, d.ctr);
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(BLK) k_state_equilibrium(Phys ph, double rho, 
   WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
   targets<BLK>(ux, uy, uz, T, m);
   gaussian_guess<BLK>(ux, uy, uz, T, lam);
-  const NewtonResult nr = newton<BLK, false>(w, ph, maxit);
+  const NewtonResult nr = newton<BLK, false>(w, ph, maxit, false);
   for (int i = 0; i < Q; ++i) {
     out78[i] = rho * F[i];
     out78[Q + i] = ph.cg * T * rho * F[i];

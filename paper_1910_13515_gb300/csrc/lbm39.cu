@@ -42,7 +42,7 @@ AuxLayout aux_layout(long long N) {
   const long long Np = plane_stride(N);
   AuxLayout a;
   size_t off = 0;
-  a.lam = off; off = align256(off + sizeof(double) * NM * Np);
+  a.lam = off; off = align256(off + sizeof(double) * SOLVER_PLANES * Np);
   a.ctr = off; off = align256(off + sizeof(unsigned long long) * 64);
   a.heq = off; off = align256(off + sizeof(double) * 2 * Q);
   a.href = off; off = align256(off + sizeof(double) * 2 * Q);
@@ -471,7 +471,7 @@ int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
 
 size_t lbm39_checkpoint_bytes(const lbm39_lattice* L) {
   if (!L) return 0;
-  return 256 + L->pop_bytes() + sizeof(double) * NM * L->Np;
+  return 256 + L->pop_bytes() + sizeof(double) * SOLVER_PLANES * L->Np;
 }
 
 int lbm39_save(lbm39_lattice* L, void* buf) {
@@ -483,7 +483,7 @@ int lbm39_save(lbm39_lattice* L, void* buf) {
   hdr[2] = (uint64_t)L->N;
   hdr[3] = (uint64_t)L->p.precision;
   char* b = static_cast<char*>(buf);
-  const size_t pb = L->pop_bytes(), lb = sizeof(double) * NM * L->Np;
+  const size_t pb = L->pop_bytes(), lb = sizeof(double) * SOLVER_PLANES * L->Np;
   CUDA_OK(cudaMemcpyAsync(b, hdr, sizeof hdr, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(b + 256, L->pop, pb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(b + 256 + pb, L->desc.lam, lb, cudaMemcpyDefault, L->stream));
@@ -499,7 +499,7 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   CUDA_OK(cudaStreamSynchronize(L->stream));
   if (hdr[0] != CKPT_MAGIC || hdr[2] != (uint64_t)L->N || hdr[3] != (uint64_t)L->p.precision)
     return LBM39_ERR_ARG;
-  const size_t pb = L->pop_bytes(), lb = sizeof(double) * NM * L->Np;
+  const size_t pb = L->pop_bytes(), lb = sizeof(double) * SOLVER_PLANES * L->Np;
   CUDA_OK(cudaMemcpyAsync(L->pop, b + 256, pb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemcpyAsync(L->desc.lam, b + 256 + pb, lb, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));

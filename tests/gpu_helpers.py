@@ -48,7 +48,7 @@ def patch_from_checkpoint(L, buf, cx, cy, cz, r=3):
     Np = (N + 63) // 64 * 64
     body = buf[256:].view(torch.float64)
     pops = body[: 78 * Np].view(78, Np)
-    lams = body[78 * Np: 78 * Np + 13 * Np].view(13, Np)
+    lams = body[78 * Np: 78 * Np + 13 * Np].view(13, Np)  # multipliers lead the solver state
     rz = r if nz > 1 else 0
     xs = [(cx + d) % nx for d in range(-r, r + 1)]
     ys = [(cy + d) % ny for d in range(-r, r + 1)]

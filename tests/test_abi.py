@@ -57,7 +57,7 @@ def test_default_params_and_sizes(C):
     N = 480
     Np = (N + 63) // 64 * 64
     assert pop_b == 78 * 8 * Np
-    assert aux_b >= 13 * 8 * Np
+    assert aux_b >= 52 * 8 * Np
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("tau", 0.4),
