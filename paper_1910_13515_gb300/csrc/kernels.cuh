@@ -50,9 +50,11 @@ struct Coord {
   int x, y, z;
 };
 
+// (cell < 2^31: lattices are limited to 2^31 - 1 cells)
 __device__ __forceinline__ Coord coord_of(const Desc& d, long long cell) {
-  const long long yz = cell / d.nx;
-  return Coord{int(cell - yz * d.nx), int(yz % d.ny), int(yz / d.ny)};
+  const int c = (int)cell;
+  const int yz = c / d.nx;
+  return Coord{c - yz * d.nx, yz % d.ny, yz / d.ny};
 }
 
 __device__ __forceinline__ int wrap(int a, int n) {
@@ -62,22 +64,36 @@ __device__ __forceinline__ int wrap(int a, int n) {
 
 // Index of the cell at x + (dx, dy, dz) with periodic wrap of every axis
 // (non-periodic axes carry boundary layers, so fluid cells never wrap there).
+// Every index is below 2^31, so the 21 terms are 32-bit.
 struct Nbr {
-  int xs[7];
-  long long ys[7], zs[7];
+  int xs[7], ys[7], zs[7];
   __device__ __forceinline__ Nbr() {}
   __device__ __forceinline__ Nbr(const Desc& d, Coord c) {
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       xs[s] = wrap(c.x + s - 3, d.nx);
-      ys[s] = (long long)wrap(c.y + s - 3, d.ny) * d.nx;
-      zs[s] = (long long)wrap(c.z + s - 3, d.nz) * d.nx * d.ny;
+      ys[s] = wrap(c.y + s - 3, d.ny) * d.nx;
+      zs[s] = wrap(c.z + s - 3, d.nz) * d.nx * d.ny;
     }
   }
   __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
-    return xs[dx + 3] + ys[dy + 3] + zs[dz + 3];
+    return (long long)(xs[dx + 3] + ys[dy + 3] + zs[dz + 3]);
   }
 };
+
+// The neighbour table of `cell`, built from a copy of the index that the
+// compiler cannot see through: a table built before the constraint solve is
+// then not kept in registers across it (the odd pass builds it twice).
+template <bool ODD>
+__device__ __forceinline__ Nbr fresh_nbr(const Desc& d, long long cell) {
+  Nbr nb;
+  if constexpr (ODD) {
+    long long c = cell;
+    asm volatile("" : "+l"(c));
+    nb = Nbr(d, coord_of(d, c));
+  }
+  return nb;
+}
 
 // Pre-collision populations of one distribution (base 0: f, Q: g) of fluid
 // cell `cell` at the lattice's current time: own slots at even time, the odd
@@ -281,18 +297,16 @@ template <bool ODD, class P, int BLK>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
-  Nbr nb;
   unsigned long long bits = 0;
   if constexpr (ODD) {
-    nb = Nbr(d, coord_of(d, cell));
     if (d.bounce) bits = d.bounce[cell];
   }
-  const Macro M = gather_moments<ODD, P>(d, cell, nb, bits);
+  const Macro M = gather_moments<ODD, P>(d, cell, fresh_nbr<ODD>(d, cell), bits);
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
   const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit, true);
   store_solver_state<BLK>(d, cell, w);
-  const int branch = relax_push<ODD, P, BLK>(d, cell, nb, bits, M, F);
+  const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, cell), bits, M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
   atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
