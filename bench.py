@@ -472,7 +472,7 @@ def main():
                            BYTES_PER_UPDATE[args.precision] / 2 * N / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": args.steps * (2 if L.has_ghosts else 1),
+            "gpu_launches": args.steps * (2 if L.has_fills else 1),
             "cpu_baseline": cpu,
             "precision_form": form,
             "kernel_hash": kernel_source_hash(),

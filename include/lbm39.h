@@ -12,7 +12,8 @@
  * bounce-back); Sec. 5 the per-cell equilibrium step table.
  *
  * Conventions shared by every call
- * - A lattice has nx*ny*nz cells, x fastest: cell = x + nx*(y + ny*z).
+ * - A lattice has nx*ny*nz cells, x fastest: cell = x + nx*(y + ny*z), and
+ *   at most 2^31 - 64 cells (larger lattices are rejected with LBM39_ERR_ARG).
  * - Scalar fields are arrays of N = nx*ny*nz float64; velocity fields are 3
  *   consecutive planes of N (u_x, then u_y, then u_z).
  * - Temperatures are lattice temperatures: p = rho*T, c_s = sqrt(gamma*T).

@@ -32,7 +32,6 @@ struct Desc {
   double* lam;                        // 13 planes of multipliers kept between steps, then
                                       // 39 planes of F_i = exp(Phi lam) at them
   const uint8_t* mask;                // nullptr: every cell fluid, all axes periodic
-  const unsigned long long* bounce;   // bit i: the source x - xi_i is solid (nullptr: none)
   unsigned long long* ctr;            // counters (CTR_*)
   const void* free_store;             // 78 stored values (P) of a freestream cell
   const double* heq_inf;              // 78 far-field equilibrium populations (FP64)
@@ -57,8 +56,10 @@ __device__ __forceinline__ Coord coord_of(const Desc& d, long long cell) {
   return Coord{c - yz * d.nx, yz % d.ny, yz / d.ny};
 }
 
+// a mod n for a in [-3, n + 2]: one conditional correction when n >= 3.
 __device__ __forceinline__ int wrap(int a, int n) {
-  int r = a % n;
+  if (n >= 3) return a < 0 ? a + n : (a >= n ? a - n : a);
+  const int r = a % n;
   return r < 0 ? r + n : r;
 }
 
@@ -76,31 +77,32 @@ struct Nbr {
       zs[s] = wrap(c.z + s - 3, d.nz) * d.nx * d.ny;
     }
   }
-  __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
-    return (long long)(xs[dx + 3] + ys[dy + 3] + zs[dz + 3]);
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return xs[dx + 3] + ys[dy + 3] + zs[dz + 3];
   }
 };
 
-// The neighbour table of `cell`, built from a copy of the index that the
-// compiler cannot see through: a table built before the constraint solve is
-// then not kept in registers across it (the odd pass builds it twice).
+// The neighbour table of the cell at c, built from a copy of the coordinates
+// that the compiler cannot see through: a table built before the constraint
+// solve is then not kept in registers across it (the odd pass builds it twice).
 template <bool ODD>
-__device__ __forceinline__ Nbr fresh_nbr(const Desc& d, long long cell) {
+__device__ __forceinline__ Nbr fresh_nbr(const Desc& d, Coord c) {
   Nbr nb;
   if constexpr (ODD) {
-    long long c = cell;
-    asm volatile("" : "+l"(c));
-    nb = Nbr(d, coord_of(d, c));
+    asm volatile("" : "+r"(c.x), "+r"(c.y), "+r"(c.z));
+    nb = Nbr(d, c);
   }
   return nb;
 }
 
 // Pre-collision populations of one distribution (base 0: f, Q: g) of fluid
 // cell `cell` at the lattice's current time: own slots at even time, the odd
-// gather (with bounce-back) at odd time.
+// gather from (x - xi_i, slot opp i) at odd time.  Where x - xi_i is solid,
+// that slot holds the bounced population (bounce_even_cell), so the gather
+// has no per-direction branch.
 template <bool ODD, class P>
-__device__ __forceinline__ void gather(const Desc& d, long long cell, const Nbr& nb,
-                                       unsigned long long bits, int base, P (&h)[Q]) {
+__device__ __forceinline__ void gather(const Desc& d, long long cell, const Nbr& nb, int base,
+                                       P (&h)[Q]) {
   const P* __restrict__ pop = static_cast<const P*>(d.pop);
   static_for<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -108,27 +110,23 @@ __device__ __forceinline__ void gather(const Desc& d, long long cell, const Nbr&
       h[i] = pop[(long long)(base + i) * d.Np + cell];
     } else {
       constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
-      const long long src = ((bits >> i) & 1ull)
-                                ? (long long)(base + i) * d.Np + cell
-                                : (long long)(base + opp(i)) * d.Np + nb.at(-cx, -cy, -cz);
-      h[i] = pop[src];
+      h[i] = pop[(long long)(base + opp(i)) * d.Np + nb.at(-cx, -cy, -cz)];
     }
   });
 }
 
-// Post-collision population h*_i of fluid cell `cell` into its AA slot.
+// Post-collision population h*_i of fluid cell `cell` into its AA slot: own
+// slot opp i at even time, (x + xi_i, slot i) at odd time (a solid x + xi_i
+// hands it back to x afterwards: bounce_odd_cell).
 template <bool ODD, class P, int i>
-__device__ __forceinline__ void push(const Desc& d, long long cell, const Nbr& nb,
-                                     unsigned long long bits, int base, P v) {
+__device__ __forceinline__ void push(const Desc& d, long long cell, const Nbr& nb, int base,
+                                     P v) {
   P* __restrict__ pop = static_cast<P*>(d.pop);
   if constexpr (!ODD) {
     pop[(long long)(base + opp(i)) * d.Np + cell] = v;
   } else {
     constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
-    const long long dst = ((bits >> opp(i)) & 1ull)
-                              ? (long long)(base + opp(i)) * d.Np + cell
-                              : (long long)(base + i) * d.Np + nb.at(cx, cy, cz);
-    pop[dst] = v;
+    pop[(long long)(base + i) * d.Np + nb.at(cx, cy, cz)] = v;
   }
 }
 
@@ -139,24 +137,23 @@ struct Raw {
 
 // Phase A: gather each distribution in turn and take the moments (FP64).
 template <bool ODD, class P>
-__device__ __forceinline__ Raw gather_raw(const Desc& d, long long cell, const Nbr& nb,
-                                          unsigned long long bits) {
+__device__ __forceinline__ Raw gather_raw(const Desc& d, long long cell, const Nbr& nb) {
   Raw r;
   double gs;
   if constexpr (sizeof(P) == 8) {
     P h[Q];
-    gather<ODD, P>(d, cell, nb, bits, 0, h);
+    gather<ODD, P>(d, cell, nb, 0, h);
     gen::f_moments<double>(h, r.rho, r.jx, r.jy, r.jz, r.e2);
-    gather<ODD, P>(d, cell, nb, bits, Q, h);
+    gather<ODD, P>(d, cell, nb, Q, h);
     gs = gen::g_sum<double>(h);
   } else {  // deviations: moments of h_ref (precomputed) plus those of the deviations
     P h[Q];
     double hd[Q];
-    gather<ODD, P>(d, cell, nb, bits, 0, h);
+    gather<ODD, P>(d, cell, nb, 0, h);
 #pragma unroll
     for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
     gen::f_moments<double>(hd, r.rho, r.jx, r.jy, r.jz, r.e2);
-    gather<ODD, P>(d, cell, nb, bits, Q, h);
+    gather<ODD, P>(d, cell, nb, Q, h);
 #pragma unroll
     for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
     gs = gen::g_sum<double>(hd);
@@ -168,9 +165,8 @@ __device__ __forceinline__ Raw gather_raw(const Desc& d, long long cell, const N
 }
 
 template <bool ODD, class P>
-__device__ __forceinline__ Macro gather_moments(const Desc& d, long long cell, const Nbr& nb,
-                                                unsigned long long bits) {
-  const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+__device__ __forceinline__ Macro gather_moments(const Desc& d, long long cell, const Nbr& nb) {
+  const Raw r = gather_raw<ODD, P>(d, cell, nb);
   return macro_from_moments(r.rho, r.jx, r.jy, r.jz, r.e2, d.ph.inv_2cv);
 }
 
@@ -190,7 +186,7 @@ __device__ __forceinline__ float round_float(double x) {
 // normalised equilibrium; f^eq = rho F, g^eq = (2C_v - D) T rho F.
 template <bool ODD, class P, int BLK>
 __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const Nbr& nb,
-                                          unsigned long long bits, const Macro& M, WS<BLK> F) {
+                                          const Macro& M, WS<BLK> F) {
   const Phys& ph = d.ph;
   const double rho = M.rho;
   const float rho32 = trunc_float(rho);
@@ -198,7 +194,7 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
   double eps;
   if constexpr (sizeof(P) == 8) {
     P f[Q];
-    gather<ODD, P>(d, cell, nb, bits, 0, f);
+    gather<ODD, P>(d, cell, nb, 0, f);
     // FP32 estimate of 39 eps from float views (absolute error < 2.5e-5),
     // FP64 value when that cannot decide the branch of Eq. (alpha)
     float s32 = 0.0f;
@@ -221,20 +217,20 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     const double omega = 1.0 / (ph.tau * alpha);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      push<ODD, P, i>(d, cell, nb, bits, 0, fma(-omega, fma(-rho, F[i], f[i]), f[i]));
+      push<ODD, P, i>(d, cell, nb, 0, fma(-omega, fma(-rho, F[i], f[i]), f[i]));
     });
     P g[Q];
-    gather<ODD, P>(d, cell, nb, bits, Q, g);
+    gather<ODD, P>(d, cell, nb, Q, g);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      push<ODD, P, i>(d, cell, nb, bits, Q, fma(-omega, fma(-cgr, F[i], g[i]), g[i]));
+      push<ODD, P, i>(d, cell, nb, Q, fma(-omega, fma(-cgr, F[i], g[i]), g[i]));
     });
   } else {
     // precision form: h~ = h - h_ref stored in FP32; equilibrium deviation
     // h^eq - h_ref formed in FP64 and rounded; sensor and BGK in FP32.
     const double* __restrict__ href = d.href;
     P f[Q];
-    gather<ODD, P>(d, cell, nb, bits, 0, f);
+    gather<ODD, P>(d, cell, nb, 0, f);
     float s32 = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -246,17 +242,17 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
     const float omega = (float)(1.0 / (ph.tau * alpha));
     P f2[Q];
-    gather<ODD, P>(d, cell, nb, bits, 0, f2);  // the stored values again (cached)
+    gather<ODD, P>(d, cell, nb, 0, f2);  // the stored values again (cached)
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      push<ODD, P, i>(d, cell, nb, bits, 0, fmaf(-omega, f[i], f2[i]));
+      push<ODD, P, i>(d, cell, nb, 0, fmaf(-omega, f[i], f2[i]));
     });
     P g[Q];
-    gather<ODD, P>(d, cell, nb, bits, Q, g);
+    gather<ODD, P>(d, cell, nb, Q, g);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const float qg = round_float(fma(cgr, F[i], -__ldg(href + Q + i)));
-      push<ODD, P, i>(d, cell, nb, bits, Q, fmaf(-omega, g[i] - qg, g[i]));
+      push<ODD, P, i>(d, cell, nb, Q, fmaf(-omega, g[i] - qg, g[i]));
     });
   }
   return alpha_branch(eps);
@@ -297,16 +293,14 @@ template <bool ODD, class P, int BLK>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
-  unsigned long long bits = 0;
-  if constexpr (ODD) {
-    if (d.bounce) bits = d.bounce[cell];
-  }
-  const Macro M = gather_moments<ODD, P>(d, cell, fresh_nbr<ODD>(d, cell), bits);
+  Coord c{0, 0, 0};
+  if constexpr (ODD) c = coord_of(d, cell);
+  const Macro M = gather_moments<ODD, P>(d, cell, fresh_nbr<ODD>(d, c));
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
   const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit, true);
   store_solver_state<BLK>(d, cell, w);
-  const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, cell), bits, M, F);
+  const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, c), M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
   atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
@@ -394,25 +388,50 @@ __global__ void __launch_bounds__(BLK) k_state_equilibrium(Phys ph, double rho, 
   if (nr.failed) atomicAdd(failed, 1ull);
 }
 
-// Bit i of bounce[cell]: the source x - xi_i of fluid cell `cell` is solid.
-__global__ void k_bounce_bits(Desc d, unsigned long long* bounce) {
-  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= d.N) return;
-  unsigned long long b = 0;
-  if (d.mask[cell] == MASK_FLUID) {
-    const Nbr nb(d, coord_of(d, cell));
-    for (int i = 0; i < Q; ++i)
-      if (d.mask[nb.at(-kCX[i], -kCY[i], -kCZ[i])] == MASK_SOLID) b |= 1ull << i;
-  }
-  bounce[cell] = b;
-}
-
 // After an even pass: freestream cells hold the far-field post-collision
 // populations and outflow cells a copy of the cell with x clamped into
 // [3, nx-4], both in the reversed (post-collision) layout the odd pass reads.
+// Half-way bounce-back (Sec. 4) after an even pass.  The even pass leaves
+// f*_opp(i)(x) of a fluid cell x in its slot i; the odd pass gathers f_i(x)
+// from (x - xi_i, slot opp i), which for x = s + xi_i is (s, slot opp i): the
+// solid cell s copies the value there.  Each of these slots has one writer.
+template <class P>
+__device__ __forceinline__ void bounce_even_cell(const Desc& d, long long s) {
+  P* pop = static_cast<P*>(d.pop);
+  const Nbr nb(d, coord_of(d, s));
+  for (int i = 0; i < Q; ++i) {
+    const long long x = nb.at(kCX[i], kCY[i], kCZ[i]);
+    if (d.mask[x] != MASK_FLUID) continue;
+    const int o = opp(i);
+    pop[(long long)o * d.Np + s] = pop[(long long)i * d.Np + x];
+    pop[(long long)(Q + o) * d.Np + s] = pop[(long long)(Q + i) * d.Np + x];
+  }
+}
+
+// Half-way bounce-back after an odd pass: fluid cell x = s - xi_i pushed
+// f*_i(x) into (s, slot i); it returns as f_opp(i)(x), which the even pass
+// reads from (x, slot opp i) -- a slot no push writes, since its source
+// x - xi_opp(i) = s is solid.
+template <class P>
+__device__ __forceinline__ void bounce_odd_cell(const Desc& d, long long s) {
+  P* pop = static_cast<P*>(d.pop);
+  const Nbr nb(d, coord_of(d, s));
+  for (int i = 0; i < Q; ++i) {
+    const long long x = nb.at(-kCX[i], -kCY[i], -kCZ[i]);
+    if (d.mask[x] != MASK_FLUID) continue;
+    const int o = opp(i);
+    pop[(long long)o * d.Np + x] = pop[(long long)i * d.Np + s];
+    pop[(long long)(Q + o) * d.Np + x] = pop[(long long)(Q + i) * d.Np + s];
+  }
+}
+
 template <class P>
 __device__ __forceinline__ void fill_even_cell(const Desc& d, long long cell) {
   const uint8_t mk = d.mask[cell];
+  if (mk == MASK_SOLID) {
+    bounce_even_cell<P>(d, cell);
+    return;
+  }
   if (mk != MASK_FREE && mk != MASK_OUT) return;
   P* pop = static_cast<P*>(d.pop);
   const P* fs = static_cast<const P*>(d.free_store);
@@ -437,11 +456,17 @@ __device__ __forceinline__ void fill_even_cell(const Desc& d, long long cell) {
 
 // After an odd pass: fluid slots whose source is a freestream or outflow cell
 // receive what that cell streamed: the far-field equilibrium, or the
-// post-collision population of the clamped cell c (which c pushed into
-// slot (c + xi_i, i), or bounced into (c, opp i) if c + xi_i is solid).
+// post-collision population of the clamped cell c, which c pushed into slot
+// (c + xi_i, i) (also when c + xi_i is solid: bounce_odd_cell only copies it
+// on).  Solid cells do their bounce-back copies.
 template <class P>
 __device__ __forceinline__ void fill_odd_cell(const Desc& d, long long cell) {
-  if (d.mask[cell] != MASK_FLUID) return;
+  const uint8_t mk = d.mask[cell];
+  if (mk == MASK_SOLID) {
+    bounce_odd_cell<P>(d, cell);
+    return;
+  }
+  if (mk != MASK_FLUID) return;
   const Coord c = coord_of(d, cell);
   const bool near = (!d.per[0] && (c.x < 6 || c.x >= d.nx - 6)) ||
                     (!d.per[1] && (c.y < 6 || c.y >= d.ny - 6)) ||
@@ -465,7 +490,7 @@ __device__ __forceinline__ void fill_odd_cell(const Desc& d, long long cell) {
         const long long t = (long long)wrap(ccc.x + kCX[i], d.nx) +
                             (long long)d.nx * (wrap(ccc.y + kCY[i], d.ny) +
                                                (long long)d.ny * wrap(ccc.z + kCZ[i], d.nz));
-        src = (d.mask[t] == MASK_SOLID) ? (long long)opp(i) * d.Np + cc : jf + t;
+        src = jf + t;
       }
     }
     if (src < 0) {
@@ -501,12 +526,8 @@ __global__ void k_macros(Desc d, double* rho, double* u, long long us, double* T
   Macro M{0, 0, 0, 0, 0};
   if (d.mask == nullptr || d.mask[cell] == MASK_FLUID) {
     Nbr nb;
-    unsigned long long bits = 0;
-    if constexpr (ODD) {
-      nb = Nbr(d, coord_of(d, cell));
-      if (d.bounce) bits = d.bounce[cell];
-    }
-    M = gather_moments<ODD, P>(d, cell, nb, bits);
+    if constexpr (ODD) nb = Nbr(d, coord_of(d, cell));
+    M = gather_moments<ODD, P>(d, cell, nb);
   }
   if (rho) rho[r] = M.rho;
   if (u) { u[r] = M.ux; u[us + r] = M.uy; u[2 * us + r] = M.uz; }
@@ -525,12 +546,8 @@ __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
        cell += (long long)gridDim.x * BLK) {
     if (d.mask != nullptr && d.mask[cell] != MASK_FLUID) continue;
     Nbr nb;
-    unsigned long long bits = 0;
-    if constexpr (ODD) {
-      nb = Nbr(d, coord_of(d, cell));
-      if (d.bounce) bits = d.bounce[cell];
-    }
-    const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+    if constexpr (ODD) nb = Nbr(d, coord_of(d, cell));
+    const Raw r = gather_raw<ODD, P>(d, cell, nb);
     acc[0] += r.rho;
     acc[1] += r.jx;
     acc[2] += r.jy;

@@ -31,7 +31,7 @@ constexpr uint64_t CKPT_MAGIC = 0x3933424d4c424c31ull;
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct AuxLayout {
-  size_t lam, ctr, heq, href, fstore, bounce, partials, result, stage, total;
+  size_t lam, ctr, heq, href, fstore, partials, result, stage, total;
 };
 
 long long plane_stride(long long N) { return (N + 63) / 64 * 64; }
@@ -47,7 +47,6 @@ AuxLayout aux_layout(long long N) {
   a.heq = off; off = align256(off + sizeof(double) * 2 * Q);
   a.href = off; off = align256(off + sizeof(double) * 2 * Q);
   a.fstore = off; off = align256(off + sizeof(double) * 2 * Q);
-  a.bounce = off; off = align256(off + sizeof(unsigned long long) * Np);
   a.partials = off; off = align256(off + sizeof(double) * 5 * RED_BLOCKS);
   a.result = off; off = align256(off + sizeof(double) * 8);
   a.stage = off; off = align256(off + sizeof(double) * 6 * std::min(N, STAGE_CELLS));
@@ -59,7 +58,7 @@ bool params_ok(const lbm39_params* p) {
   if (!p) return false;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (N > (1LL << 31) - 1) return false;
+  if (N > (1LL << 31) - 64) return false;  // plane stride (N rounded up to 64) stays 32-bit
   if (!(p->gamma > 1.0) || !(p->tau >= 0.5) || !(p->newton_tol > 0.0)) return false;
   if (p->newton_maxit < 1 || p->newton_maxit > 1000 || p->newton_min_upd < 0 ||
       p->init_maxit < 1 || p->init_maxit > 10000)
@@ -82,7 +81,8 @@ struct lbm39_lattice {
   char* aux = nullptr;
   AuxLayout lay{};
   const uint8_t* mask = nullptr;
-  bool ghosts = false;
+  bool ghosts = false;  // freestream or outflow cells
+  bool fills = false;   // ghosts or solids: the fill kernels run after each pass
   bool mixed = false;
   cudaStream_t stream = nullptr;
   long long t = 0;
@@ -108,10 +108,10 @@ struct Launch {
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
     if (!odd) {
       k_step<false, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
-      if (L->ghosts) k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+      if (L->fills) k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
     } else {
       k_step<true, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
-      if (L->ghosts) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+      if (L->fills) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
     }
   }
   static void init(lbm39_lattice* L, const double* rho, const double* u, long long us,
@@ -257,13 +257,13 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   L->lay = aux_layout(N);
   L->mask = mask_dev;
   L->ghosts = ghosts;
+  L->fills = ghosts || solids;
   L->mixed = p->precision == LBM39_MIXED;
   L->stream = stream;
   Desc& d = L->desc;
   d.pop = pop_buf;
   d.lam = reinterpret_cast<double*>(L->aux + L->lay.lam);
   d.mask = mask_dev;
-  d.bounce = nullptr;
   d.ctr = L->ctr();
   d.heq_inf = reinterpret_cast<const double*>(L->aux + L->lay.heq);
   d.href = reinterpret_cast<const double*>(L->aux + L->lay.href);
@@ -313,12 +313,6 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
       delete L;
       return LBM39_ERR_CUDA;
     }
-  }
-  if (solids) {
-    unsigned long long* b = reinterpret_cast<unsigned long long*>(L->aux + L->lay.bounce);
-    k_bounce_bits<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(d, b);
-    if (last_launch() != LBM39_OK) { delete L; return LBM39_ERR_CUDA; }
-    d.bounce = b;
   }
   if (cudaStreamSynchronize(stream) != cudaSuccess) { delete L; return LBM39_ERR_CUDA; }
   *out = L;
@@ -671,7 +665,7 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
     B->lats.push_back(L);
     B->tend.push_back(t_end[j]);
     for (long long c = 0; c < L->N; c += BLK) B->hT.push_back(Tile{j, 0, c});
-    if (L->ghosts)
+    if (L->fills)
       for (long long c = 0; c < L->N; c += 256) B->hF.push_back(Tile{j, 0, c});
   }
   if ((long long)B->hT.size() > B->maxtiles || (long long)B->hF.size() > B->maxftiles)
@@ -755,12 +749,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_conserved_chunks(Desc d, do
   for (long long cell = c0 + threadIdx.x; cell < c1; cell += NOALLOC_THREADS) {
     if (d.mask != nullptr && d.mask[cell] != MASK_FLUID) continue;
     Nbr nb;
-    unsigned long long bits = 0;
-    if constexpr (ODD) {
-      nb = Nbr(d, coord_of(d, cell));
-      if (d.bounce) bits = d.bounce[cell];
-    }
-    const Raw r = gather_raw<ODD, P>(d, cell, nb, bits);
+    if constexpr (ODD) nb = Nbr(d, coord_of(d, cell));
+    const Raw r = gather_raw<ODD, P>(d, cell, nb);
     acc[0] += r.rho;
     acc[1] += r.jx;
     acc[2] += r.jy;

@@ -52,8 +52,9 @@ class Lattice:
         self.pop = torch.empty((pop_b + 7) // 8, dtype=torch.float64, device=self.device)
         self.aux = torch.empty((aux_b + 7) // 8, dtype=torch.float64, device=self.device)
         self.mask = None
-        self.has_ghosts = mask is not None and bool(
-            np.isin(np.asarray(mask), (2, 3)).any())
+        # freestream, outflow or solid cells: the library runs a fill kernel after each pass
+        self.has_fills = mask is not None and bool(
+            np.isin(np.asarray(mask), (1, 2, 3)).any())
         if mask is not None:
             self.mask = torch.as_tensor(np.ascontiguousarray(mask, np.uint8).reshape(-1),
                                         device=self.device)

@@ -76,6 +76,19 @@ def test_mixed_sod_l1_error_vs_oracle(mod):
     assert max(err) <= 1e-4, err
 
 
+def test_mixed_obstacle_box_l1_error_vs_oracle(mod):
+    """Solid block across the periodic boundary: bounce-back in the precision form."""
+    C, Lattice = mod
+    s = inputs.box(seed=5, shape=(7, 10, 12))
+    s.mask.reshape(7, 10, 12)[2:4, 3:6, [10, 11, 0]] = 1
+    L = Lattice.from_setup(s, precision=C.LBM39_MIXED)
+    L.step(60)
+    assert L.sync() == 0
+    st, fo = run_oracle(s, 60)
+    err = l1_rel(L.read_numpy(), o.macros(st), s.mask)
+    assert max(err) <= 1e-4, err
+
+
 def test_mixed_conservation_drift(mod):
     """Periodic box, 1000 steps: relative drift of mass and energy and momentum drift
     relative to the mass (all FP64 sums of the stored state)."""
