@@ -258,31 +258,31 @@ __device__ __forceinline__ void moments(const A& F, T (&s)[13], T (&J)[91]) {
   const T w13_0_1 = F[33] - F[34];
   const T h300_0 = w13_0_0;
   const T h300_x = w13_0_1;
-  const T M000_0 = h000_0 + h001_0 + h002_0 + h003_0 + h010_0 + h020_0 + h022_0 + h030_0 + h100_0 + h111_0 + h200_0 + h202_0 + h220_0 + h300_0;
-  const T M001_0 = fma(T(2), h202_z, fma(T(2), h022_z, fma(T(3), h003_z, fma(T(2), h002_z, h001_z + h111_z))));
-  const T M010_0 = fma(T(2), h220_y, fma(T(3), h030_y, fma(T(2), h022_y, fma(T(2), h020_y, h010_y + h111_y))));
-  const T M100_0 = fma(T(3), h300_x, fma(T(2), h220_x, fma(T(2), h202_x, fma(T(2), h200_x, h100_x + h111_x))));
-  const T M002_0 = fma(T(4), h202_0, fma(T(4), h022_0, fma(T(9), h003_0, fma(T(4), h002_0, h001_0 + h111_0))));
+  const T M000_0 = (((h000_0 + h010_0 + h100_0 + h220_0) + (h001_0 + h020_0 + h111_0 + h300_0)) + ((h002_0 + h022_0 + h200_0) + (h003_0 + h030_0 + h202_0)));
+  const T M001_0 = ((fma(T(2), h022_z, fma(T(2), h002_z, h001_z))) + (fma(T(2), h202_z, fma(T(3), h003_z, h111_z))));
+  const T M010_0 = ((fma(T(3), h030_y, fma(T(2), h020_y, h010_y))) + (fma(T(2), h220_y, fma(T(2), h022_y, h111_y))));
+  const T M100_0 = ((fma(T(2), h220_x, fma(T(2), h200_x, h100_x))) + (fma(T(3), h300_x, fma(T(2), h202_x, h111_x))));
+  const T M002_0 = ((fma(T(4), h022_0, fma(T(4), h002_0, h001_0))) + (fma(T(4), h202_0, fma(T(9), h003_0, h111_0))));
   const T M011_0 = fma(T(4), h022_yz, h111_yz);
-  const T M020_0 = fma(T(4), h220_0, fma(T(9), h030_0, fma(T(4), h022_0, fma(T(4), h020_0, h010_0 + h111_0))));
+  const T M020_0 = ((fma(T(9), h030_0, fma(T(4), h020_0, h010_0))) + (fma(T(4), h220_0, fma(T(4), h022_0, h111_0))));
   const T M101_0 = fma(T(4), h202_xz, h111_xz);
   const T M110_0 = fma(T(4), h220_xy, h111_xy);
-  const T M200_0 = fma(T(9), h300_0, fma(T(4), h220_0, fma(T(4), h202_0, fma(T(4), h200_0, h100_0 + h111_0))));
-  const T M003_0 = fma(T(8), h202_z, fma(T(8), h022_z, fma(T(27), h003_z, fma(T(8), h002_z, h001_z + h111_z))));
+  const T M200_0 = ((fma(T(4), h220_0, fma(T(4), h200_0, h100_0))) + (fma(T(9), h300_0, fma(T(4), h202_0, h111_0))));
+  const T M003_0 = ((fma(T(8), h022_z, fma(T(8), h002_z, h001_z))) + (fma(T(8), h202_z, fma(T(27), h003_z, h111_z))));
   const T M012_0 = fma(T(8), h022_y, h111_y);
   const T M021_0 = fma(T(8), h022_z, h111_z);
-  const T M030_0 = fma(T(8), h220_y, fma(T(27), h030_y, fma(T(8), h022_y, fma(T(8), h020_y, h010_y + h111_y))));
+  const T M030_0 = ((fma(T(27), h030_y, fma(T(8), h020_y, h010_y))) + (fma(T(8), h220_y, fma(T(8), h022_y, h111_y))));
   const T M102_0 = fma(T(8), h202_x, h111_x);
   const T M111_0 = h111_xyz;
   const T M120_0 = fma(T(8), h220_x, h111_x);
   const T M201_0 = fma(T(8), h202_z, h111_z);
   const T M210_0 = fma(T(8), h220_y, h111_y);
-  const T M300_0 = fma(T(27), h300_x, fma(T(8), h220_x, fma(T(8), h202_x, fma(T(8), h200_x, h100_x + h111_x))));
-  const T M004_0 = fma(T(16), h202_0, fma(T(16), h022_0, fma(T(81), h003_0, fma(T(16), h002_0, h001_0 + h111_0))));
+  const T M300_0 = ((fma(T(8), h220_x, fma(T(8), h200_x, h100_x))) + (fma(T(27), h300_x, fma(T(8), h202_x, h111_x))));
+  const T M004_0 = ((fma(T(16), h022_0, fma(T(16), h002_0, h001_0))) + (fma(T(16), h202_0, fma(T(81), h003_0, h111_0))));
   const T M013_0 = fma(T(16), h022_yz, h111_yz);
   const T M022_0 = fma(T(16), h022_0, h111_0);
   const T M031_0 = fma(T(16), h022_yz, h111_yz);
-  const T M040_0 = fma(T(16), h220_0, fma(T(81), h030_0, fma(T(16), h022_0, fma(T(16), h020_0, h010_0 + h111_0))));
+  const T M040_0 = ((fma(T(81), h030_0, fma(T(16), h020_0, h010_0))) + (fma(T(16), h220_0, fma(T(16), h022_0, h111_0))));
   const T M103_0 = fma(T(16), h202_xz, h111_xz);
   const T M112_0 = h111_xy;
   const T M121_0 = h111_xz;
@@ -292,32 +292,32 @@ __device__ __forceinline__ void moments(const A& F, T (&s)[13], T (&J)[91]) {
   const T M220_0 = fma(T(16), h220_0, h111_0);
   const T M301_0 = fma(T(16), h202_xz, h111_xz);
   const T M310_0 = fma(T(16), h220_xy, h111_xy);
-  const T M400_0 = fma(T(81), h300_0, fma(T(16), h220_0, fma(T(16), h202_0, fma(T(16), h200_0, h100_0 + h111_0))));
-  const T M001_1 = fma(T(16), h202_z, fma(T(3), h111_z, fma(T(16), h022_z, fma(T(27), h003_z, fma(T(8), h002_z, h001_z)))));
-  const T M010_1 = fma(T(16), h220_y, fma(T(3), h111_y, fma(T(27), h030_y, fma(T(16), h022_y, fma(T(8), h020_y, h010_y)))));
-  const T M100_1 = fma(T(27), h300_x, fma(T(16), h220_x, fma(T(16), h202_x, fma(T(8), h200_x, fma(T(3), h111_x, h100_x)))));
-  const T M002_1 = fma(T(32), h202_0, fma(T(3), h111_0, fma(T(32), h022_0, fma(T(81), h003_0, fma(T(16), h002_0, h001_0)))));
+  const T M400_0 = ((fma(T(16), h220_0, fma(T(16), h200_0, h100_0))) + (fma(T(81), h300_0, fma(T(16), h202_0, h111_0))));
+  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, T(27) * h003_z)));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, T(16) * h022_y)));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, T(8) * h200_x)));
+  const T M002_1 = ((fma(T(32), h202_0, fma(T(32), h022_0, fma(T(16), h002_0, h001_0)))) + (fma(T(3), h111_0, T(81) * h003_0)));
   const T M011_1 = fma(T(3), h111_yz, T(32) * h022_yz);
-  const T M020_1 = fma(T(32), h220_0, fma(T(3), h111_0, fma(T(81), h030_0, fma(T(32), h022_0, fma(T(16), h020_0, h010_0)))));
+  const T M020_1 = ((fma(T(32), h220_0, fma(T(81), h030_0, fma(T(16), h020_0, h010_0)))) + (fma(T(3), h111_0, T(32) * h022_0)));
   const T M101_1 = fma(T(32), h202_xz, T(3) * h111_xz);
   const T M110_1 = fma(T(32), h220_xy, T(3) * h111_xy);
-  const T M200_1 = fma(T(81), h300_0, fma(T(32), h220_0, fma(T(32), h202_0, fma(T(16), h200_0, fma(T(3), h111_0, h100_0)))));
-  const T M003_1 = fma(T(64), h202_z, fma(T(3), h111_z, fma(T(64), h022_z, fma(T(243), h003_z, fma(T(32), h002_z, h001_z)))));
+  const T M200_1 = ((fma(T(81), h300_0, fma(T(32), h202_0, fma(T(3), h111_0, h100_0)))) + (fma(T(32), h220_0, T(16) * h200_0)));
+  const T M003_1 = ((fma(T(64), h202_z, fma(T(64), h022_z, fma(T(32), h002_z, h001_z)))) + (fma(T(3), h111_z, T(243) * h003_z)));
   const T M012_1 = fma(T(3), h111_y, T(64) * h022_y);
   const T M021_1 = fma(T(3), h111_z, T(64) * h022_z);
-  const T M030_1 = fma(T(64), h220_y, fma(T(3), h111_y, fma(T(243), h030_y, fma(T(64), h022_y, fma(T(32), h020_y, h010_y)))));
+  const T M030_1 = ((fma(T(64), h220_y, fma(T(243), h030_y, fma(T(32), h020_y, h010_y)))) + (fma(T(3), h111_y, T(64) * h022_y)));
   const T M102_1 = fma(T(64), h202_x, T(3) * h111_x);
   const T M111_1 = T(3) * h111_xyz;
   const T M120_1 = fma(T(64), h220_x, T(3) * h111_x);
   const T M201_1 = fma(T(64), h202_z, T(3) * h111_z);
   const T M210_1 = fma(T(64), h220_y, T(3) * h111_y);
-  const T M300_1 = fma(T(243), h300_x, fma(T(64), h220_x, fma(T(64), h202_x, fma(T(32), h200_x, fma(T(3), h111_x, h100_x)))));
-  const T M002_2 = fma(T(256), h202_0, fma(T(9), h111_0, fma(T(256), h022_0, fma(T(729), h003_0, fma(T(64), h002_0, h001_0)))));
+  const T M300_1 = ((fma(T(243), h300_x, fma(T(64), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(64), h220_x, T(32) * h200_x)));
+  const T M002_2 = ((fma(T(256), h202_0, fma(T(256), h022_0, fma(T(64), h002_0, h001_0)))) + (fma(T(9), h111_0, T(729) * h003_0)));
   const T M011_2 = fma(T(9), h111_yz, T(256) * h022_yz);
-  const T M020_2 = fma(T(256), h220_0, fma(T(9), h111_0, fma(T(729), h030_0, fma(T(256), h022_0, fma(T(64), h020_0, h010_0)))));
+  const T M020_2 = ((fma(T(256), h220_0, fma(T(729), h030_0, fma(T(64), h020_0, h010_0)))) + (fma(T(9), h111_0, T(256) * h022_0)));
   const T M101_2 = fma(T(256), h202_xz, T(9) * h111_xz);
   const T M110_2 = fma(T(256), h220_xy, T(9) * h111_xy);
-  const T M200_2 = fma(T(729), h300_0, fma(T(256), h220_0, fma(T(256), h202_0, fma(T(64), h200_0, fma(T(9), h111_0, h100_0)))));
+  const T M200_2 = ((fma(T(729), h300_0, fma(T(256), h202_0, fma(T(9), h111_0, h100_0)))) + (fma(T(256), h220_0, T(64) * h200_0)));
   s[0] = M000_0;
   s[1] = M100_0;
   s[2] = M010_0;
@@ -532,19 +532,19 @@ __device__ __forceinline__ void moments_s(const A& F, T (&s)[13]) {
   const T w13_0_1 = F[33] - F[34];
   const T h300_0 = w13_0_0;
   const T h300_x = w13_0_1;
-  const T M000_0 = h000_0 + h001_0 + h002_0 + h003_0 + h010_0 + h020_0 + h022_0 + h030_0 + h100_0 + h111_0 + h200_0 + h202_0 + h220_0 + h300_0;
-  const T M001_0 = fma(T(2), h202_z, fma(T(2), h022_z, fma(T(3), h003_z, fma(T(2), h002_z, h001_z + h111_z))));
-  const T M010_0 = fma(T(2), h220_y, fma(T(3), h030_y, fma(T(2), h022_y, fma(T(2), h020_y, h010_y + h111_y))));
-  const T M100_0 = fma(T(3), h300_x, fma(T(2), h220_x, fma(T(2), h202_x, fma(T(2), h200_x, h100_x + h111_x))));
-  const T M002_0 = fma(T(4), h202_0, fma(T(4), h022_0, fma(T(9), h003_0, fma(T(4), h002_0, h001_0 + h111_0))));
+  const T M000_0 = (((h000_0 + h010_0 + h100_0 + h220_0) + (h001_0 + h020_0 + h111_0 + h300_0)) + ((h002_0 + h022_0 + h200_0) + (h003_0 + h030_0 + h202_0)));
+  const T M001_0 = ((fma(T(2), h022_z, fma(T(2), h002_z, h001_z))) + (fma(T(2), h202_z, fma(T(3), h003_z, h111_z))));
+  const T M010_0 = ((fma(T(3), h030_y, fma(T(2), h020_y, h010_y))) + (fma(T(2), h220_y, fma(T(2), h022_y, h111_y))));
+  const T M100_0 = ((fma(T(2), h220_x, fma(T(2), h200_x, h100_x))) + (fma(T(3), h300_x, fma(T(2), h202_x, h111_x))));
+  const T M002_0 = ((fma(T(4), h022_0, fma(T(4), h002_0, h001_0))) + (fma(T(4), h202_0, fma(T(9), h003_0, h111_0))));
   const T M011_0 = fma(T(4), h022_yz, h111_yz);
-  const T M020_0 = fma(T(4), h220_0, fma(T(9), h030_0, fma(T(4), h022_0, fma(T(4), h020_0, h010_0 + h111_0))));
+  const T M020_0 = ((fma(T(9), h030_0, fma(T(4), h020_0, h010_0))) + (fma(T(4), h220_0, fma(T(4), h022_0, h111_0))));
   const T M101_0 = fma(T(4), h202_xz, h111_xz);
   const T M110_0 = fma(T(4), h220_xy, h111_xy);
-  const T M200_0 = fma(T(9), h300_0, fma(T(4), h220_0, fma(T(4), h202_0, fma(T(4), h200_0, h100_0 + h111_0))));
-  const T M001_1 = fma(T(16), h202_z, fma(T(3), h111_z, fma(T(16), h022_z, fma(T(27), h003_z, fma(T(8), h002_z, h001_z)))));
-  const T M010_1 = fma(T(16), h220_y, fma(T(3), h111_y, fma(T(27), h030_y, fma(T(16), h022_y, fma(T(8), h020_y, h010_y)))));
-  const T M100_1 = fma(T(27), h300_x, fma(T(16), h220_x, fma(T(16), h202_x, fma(T(8), h200_x, fma(T(3), h111_x, h100_x)))));
+  const T M200_0 = ((fma(T(4), h220_0, fma(T(4), h200_0, h100_0))) + (fma(T(9), h300_0, fma(T(4), h202_0, h111_0))));
+  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, T(27) * h003_z)));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, T(16) * h022_y)));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, T(8) * h200_x)));
   s[0] = M000_0;
   s[1] = M100_0;
   s[2] = M010_0;
@@ -583,80 +583,22 @@ __device__ __forceinline__ void f_moments(const A& f, T& rho, T& jx, T& jy, T& j
   const T ps33 = f[33] + f[34], pd33 = f[33] - f[34];
   const T ps35 = f[35] + f[36], pd35 = f[35] - f[36];
   const T ps37 = f[37] + f[38], pd37 = f[37] - f[38];
-  T r = f[0];
-  r += ps1;
-  r += ps3;
-  r += ps5;
-  r += ps7;
-  r += ps9;
-  r += ps11;
-  r += ps13;
-  r += ps15;
-  r += ps17;
-  r += ps19;
-  r += ps21;
-  r += ps23;
-  r += ps25;
-  r += ps27;
-  r += ps29;
-  r += ps31;
-  r += ps33;
-  r += ps35;
-  r += ps37;
-  rho = r;
-  jx = fma(T(3), pd33, fma(T(2), pd27, fma(T(2), pd25, fma(T(2), pd23, fma(T(2), pd21, fma(T(2), pd15, pd1 + pd7 + pd9 + pd11 - pd13))))));
-  jy = fma(T(-2), pd23, fma(T(3), pd35, fma(T(2), pd31, fma(T(2), pd29, fma(T(2), pd21, fma(T(2), pd17, pd3 + pd7 + pd9 + pd13 - pd11))))));
-  jz = fma(T(-2), pd31, fma(T(-2), pd27, fma(T(3), pd37, fma(T(2), pd29, fma(T(2), pd25, fma(T(2), pd19, pd5 + pd7 + pd11 + pd13 - pd9))))));
-  const T sh1 = ps1 + ps3 + ps5;
-  const T sh3 = ps7 + ps9 + ps11 + ps13;
-  const T sh4 = ps15 + ps17 + ps19;
-  const T sh8 = ps21 + ps23 + ps25 + ps27 + ps29 + ps31;
-  const T sh9 = ps33 + ps35 + ps37;
-  e2f = fma(T(9), sh9, fma(T(8), sh8, fma(T(4), sh4, fma(T(3), sh3, sh1))));
+  rho = f[0] + (((((ps1 + ps3) + ps5) + (ps7 + ps9)) + (((ps11 + ps13) + ps15) + (ps17 + ps19))) + ((((ps21 + ps23) + ps25) + (ps27 + ps29)) + ((ps31 + ps33) + (ps35 + ps37))));
+  jx = (((fma(T(2), pd25, pd1 - pd13)) + (fma(T(2), pd27, fma(T(2), pd15, pd7)))) + ((fma(T(3), pd33, fma(T(2), pd21, pd9))) + (fma(T(2), pd23, pd11))));
+  jy = (((fma(T(2), pd29, pd3 - pd11)) + (fma(T(2), pd31, fma(T(2), pd17, pd7)))) + ((fma(T(3), pd35, fma(T(2), pd21, pd9))) + (fma(T(-2), pd23, pd13))));
+  jz = (((fma(T(2), pd29, pd5 - pd9)) + (fma(T(-2), pd31, fma(T(2), pd19, pd7)))) + ((fma(T(3), pd37, fma(T(2), pd25, pd11))) + (fma(T(-2), pd27, pd13))));
+  const T sh1 = ((ps1 + ps3) + ps5);
+  const T sh3 = ((ps7 + ps9) + (ps11 + ps13));
+  const T sh4 = ((ps15 + ps17) + ps19);
+  const T sh8 = (((ps21 + ps23) + ps25) + ((ps27 + ps29) + ps31));
+  const T sh9 = ((ps33 + ps35) + ps37);
+  e2f = ((fma(T(8), sh8, fma(T(3), sh3, sh1))) + (fma(T(9), sh9, T(4) * sh4)));
 }
 
 // sum g (the second population's share of the total energy).
 template <class T, class A>
 __device__ __forceinline__ T g_sum(const A& g) {
-  T gs = g[0];
-  gs += g[1];
-  gs += g[2];
-  gs += g[3];
-  gs += g[4];
-  gs += g[5];
-  gs += g[6];
-  gs += g[7];
-  gs += g[8];
-  gs += g[9];
-  gs += g[10];
-  gs += g[11];
-  gs += g[12];
-  gs += g[13];
-  gs += g[14];
-  gs += g[15];
-  gs += g[16];
-  gs += g[17];
-  gs += g[18];
-  gs += g[19];
-  gs += g[20];
-  gs += g[21];
-  gs += g[22];
-  gs += g[23];
-  gs += g[24];
-  gs += g[25];
-  gs += g[26];
-  gs += g[27];
-  gs += g[28];
-  gs += g[29];
-  gs += g[30];
-  gs += g[31];
-  gs += g[32];
-  gs += g[33];
-  gs += g[34];
-  gs += g[35];
-  gs += g[36];
-  gs += g[37];
-  gs += g[38];
+  const T gs = ((((((g[0] + g[1]) + g[2]) + (g[3] + g[4])) + (((g[5] + g[6]) + g[7]) + (g[8] + g[9]))) + ((((g[10] + g[11]) + g[12]) + (g[13] + g[14])) + (((g[15] + g[16]) + g[17]) + (g[18] + g[19])))) + (((((g[20] + g[21]) + g[22]) + (g[23] + g[24])) + (((g[25] + g[26]) + g[27]) + (g[28] + g[29]))) + ((((g[30] + g[31]) + g[32]) + (g[33] + g[34])) + ((g[35] + g[36]) + (g[37] + g[38])))));
   return gs;
 }
 

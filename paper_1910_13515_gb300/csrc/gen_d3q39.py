@@ -102,11 +102,38 @@ class Emitter:
         self.lines.append(s)
 
 
+def tree_sum(names):
+    """Balanced parenthesised sum (dependency depth log2 n instead of n)."""
+    if len(names) == 1:
+        return names[0]
+    h = (len(names) + 1) // 2
+    return f"({tree_sum(names[:h])} + {tree_sum(names[h:])})"
+
+
 def lincomb(terms, T="T"):
-    """Expression for sum c*v with integer c, as an FMA/ADD chain (no multiply by 1)."""
+    """Expression for sum c*v with integer c (no multiply by 1): for more than 4 terms, up to
+    4 independent FMA/ADD chains, each headed by a coefficient +-1 term where there is one,
+    added pairwise -- the same operation count as one chain, a quarter of its depth."""
     terms = [(c, v) for c, v in terms if c != 0]
     if not terms:
         return "T(0)".replace("T", T)
+    if len(terms) > 4:
+        k = 2 if len(terms) <= 8 else 4
+        ones = [t for t in terms if t[0] == 1] + [t for t in terms if t[0] == -1]
+        rest = [t for t in terms if abs(t[0]) != 1]
+        heads = ones[:k]
+        pool = ones[k:] + rest
+        groups = [[h] for h in heads] + [[] for _ in range(k - len(heads))]
+        for j, t in enumerate(pool):
+            groups[j % k].append(t)
+        groups = [g for g in groups if g]
+        return tree_sum([f"({lincomb_chain(g, T)})" for g in groups])
+    return lincomb_chain(terms, T)
+
+
+def lincomb_chain(terms, T):
+    """One FMA/ADD chain for sum c*v."""
+    terms = list(terms)
     # start with a coefficient-1 term if any
     terms.sort(key=lambda cv: (abs(cv[0]) != 1, cv[0] < 0))
     c, v = terms[0]
@@ -300,10 +327,7 @@ def gen_pop_moments():
     # pair sums / differences
     for i in range(1, Q, 2):
         em(f"  const T ps{i} = f[{i}] + f[{i + 1}], pd{i} = f[{i}] - f[{i + 1}];")
-    em("  T r = f[0];")
-    for i in range(1, Q, 2):
-        em(f"  r += ps{i};")
-    em("  rho = r;")
+    em(f"  rho = f[0] + {tree_sum([f'ps{i}' for i in range(1, Q, 2)])};")
     for a, nm in enumerate(("jx", "jy", "jz")):
         terms = [((CX, CY, CZ)[a][i], f"pd{i}") for i in range(1, Q, 2)]
         em(f"  {nm} = {lincomb(terms, 'T')};")
@@ -312,7 +336,7 @@ def gen_pop_moments():
         by_c2[sum(c * c for c in VEL[i])].append(f"ps{i}")
     parts = []
     for c2, lst in sorted(by_c2.items()):
-        em(f"  const T sh{c2} = {' + '.join(lst)};")
+        em(f"  const T sh{c2} = {tree_sum(lst)};")
         parts.append((c2, f"sh{c2}"))
     em(f"  e2f = {lincomb(parts, 'T')};")
     em("}")
@@ -320,9 +344,7 @@ def gen_pop_moments():
     em("// sum g (the second population's share of the total energy).")
     em("template <class T, class A>")
     em("__device__ __forceinline__ T g_sum(const A& g) {")
-    em("  T gs = g[0];")
-    for i in range(1, Q):
-        em(f"  gs += g[{i}];")
+    em(f"  const T gs = {tree_sum([f'g[{i}]' for i in range(Q)])};")
     em("  return gs;")
     em("}")
     return em.lines
