@@ -33,9 +33,8 @@ using WS = WSV<double, BLK>;
 constexpr int WS_E = 0;         // normalised equilibrium F_i (39)
 constexpr int WS_LAM = 39;      // multipliers (13)
 constexpr int WS_M = 52;        // normalised targets (13)
-constexpr int WS_LT = 65;       // trial multipliers of the Newton step (13)
-constexpr int WS_DL = 78;       // Newton direction (13)
-constexpr int WS_DOUBLES = 91;
+constexpr int WS_DL = 65;       // Newton direction (13)
+constexpr int WS_DOUBLES = 78;
 
 // Lattice-wide constants of one run.
 struct Phys {
@@ -93,19 +92,25 @@ __device__ __noinline__ void exp_all_slow(double* Fp) {
 
 // F_i = exp(sum_k lam_k phi_k(xi_i)) (Eq. discrete-equilibrium / rho) into F,
 // and the constraint residual G_k = sum_i F_i phi_k(xi_i) - m_k (Eq. constraints).
+// The evaluation point is lam - t dl (t = 0: lam itself, dl not read).
 // from_F: F already holds exp(Phi lam) (kept from the previous step), so only
 // the moments are formed -- the same numbers, bit for bit, as evaluating again.
 template <int BLK>
-__device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> F, WS<BLK> m,
-                                                 double (&G)[NM], bool from_F) {
+__device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double t, WS<BLK> F,
+                                                 WS<BLK> m, double (&G)[NM], bool from_F) {
   double x[Q];
   if (from_F) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) x[i] = F[i];
   } else {
     double l[NM];
+    if (t == 0.0) {
 #pragma unroll
-    for (int k = 0; k < NM; ++k) l[k] = lam[k];
+      for (int k = 0; k < NM; ++k) l[k] = lam[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < NM; ++k) l[k] = fma(-t, dl[k], lam[k]);
+    }
     gen::exponents(l, x);
     int wide = 0;
 #pragma unroll
@@ -251,33 +256,29 @@ struct NewtonResult {
 // exponentials.
 template <int BLK, bool MIXED>
 __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached) {
-  WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), lt = w.at(WS_LT),
-          dl = w.at(WS_DL);
-#pragma unroll
-  for (int k = 0; k < NM; ++k) lt[k] = lam[k];
+  WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), dl = w.at(WS_DL);
   int n = 0, failed = 0, ls = 0;
   bool first = true, polished = false, restore = false;
-  double t = 0.0, s0 = 0.0;
+  double t = 0.0, s0 = 0.0;  // trial point lam - t dl
   for (;;) {
     double G[NM];
-    eval_equilibrium<BLK>(lt, F, m, G, first && cached);
+    eval_equilibrium<BLK>(lam, dl, t, F, m, G, first && cached);
     if (restore) break;  // F is back at the last accepted lam after a failed line search
     if (!first && !polished && !(sum_sq(G) < s0)) {  // reject: halve the step
       if (++ls > LS_MAX) {
         failed = 1;
         restore = true;
-#pragma unroll
-        for (int k = 0; k < NM; ++k) lt[k] = lam[k];
+        t = 0.0;
         continue;
       }
       t *= 0.5;
-#pragma unroll
-      for (int k = 0; k < NM; ++k) lt[k] = fma(-t, dl[k], lam[k]);
       continue;
     }
     // accept the trial point
+    if (t != 0.0) {
 #pragma unroll
-    for (int k = 0; k < NM; ++k) lam[k] = lt[k];
+      for (int k = 0; k < NM; ++k) lam[k] = fma(-t, dl[k], lam[k]);
+    }
     if (!first) ++n;
     first = false;
     const double r = max_abs(G);
@@ -290,8 +291,6 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
     polished = r < ph.tol;
     t = 1.0;
     ls = 0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) lt[k] = lam[k] - dl[k];
   }
   return NewtonResult{n, failed};
 }
