@@ -42,7 +42,7 @@ WORKLOADS = {
 # FP64 arithmetic of one fluid-cell update as executed by the step kernel, from ncu
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL) on two workloads with different
 # Newton work: A + B * (Newton updates per cell).  See profiles/.
-FP64_FLOPS_MODEL = {"fp64": (707.0, 2559.0), "mixed": (562.0, 1014.0)}
+FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0)}
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the kernel sources they were
 # captured with; reported as null once the sources differ (profiles/ has the captures).

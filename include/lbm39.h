@@ -220,6 +220,15 @@ int lbm39_selftest_dfma(double* tflops, void* scratch, size_t scratch_bytes, voi
  * cuda_stream as in lbm39_create.  Returns after enqueueing. */
 int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void* cuda_stream);
 
+/* Check of the step's reciprocals (device arrays of n): y[i] = the FP64
+ * reciprocal used for 1/rho and the pivots of the Newton solve (Newton's
+ * method from the hardware estimate), ref[i] = CUDA's 1.0 / x[i]; y32[i] = the
+ * FP32 reciprocal of the Knudsen-sensor screen (rcp.approx.ftz.f32) of
+ * (float)x[i], ref32[i] = CUDA's 1.0f / (float)x[i].  Enqueued on cuda_stream.
+ * The paper has no counterpart: these are implementation tests. */
+int lbm39_selftest_rcp(const double* x, double* y, double* ref, float* y32, float* ref32,
+                       int64_t n, void* cuda_stream);
+
 /* Conserved sums (the conserved[] of lbm39_stats_t: mass, momentum x/y/z,
  * total energy over the fluid cells) for callers that cannot allocate device
  * memory -- for instance code that runs where cudaMalloc is unavailable or

@@ -45,7 +45,35 @@ struct Phys {
   int maxit;        // Newton updates allowed
   int min_upd;      // updates taken even from a converged warm start
   int kn_sensor;    // Eq. (alpha) on/off
+  double omega[4];  // 1 / (tau alpha) for the four branches of Eq. (alpha) (1/tau without
+                    // the sensor), formed on the host with IEEE division
 };
+
+// Reciprocals without the IEEE division sequence.
+// rcp32: the PTX instruction rcp.approx.ftz.f32 (at most 1 ulp, i.e. relative
+// error <= 2^-23, subnormals flushed to zero).
+__device__ __forceinline__ float rcp32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// rcp64: 1/d for normal d by Newton's method for the root of 1/r - d,
+// r <- r + r (1 - d r), each step squaring the relative error, two steps from
+// the hardware estimate rcp.approx.ftz.f64.  Within 2 ulp of 1/d (tested
+// against CUDA's division through lbm39_selftest_rcp).
+__device__ __forceinline__ double rcp64(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  r = fma(r, fma(-d, r, 1.0), r);
+  return fma(r, fma(-d, r, 1.0), r);
+}
+
+template <class T>
+__device__ __forceinline__ T recip(T x) {
+  if constexpr (sizeof(T) == 8) return rcp64(x);
+  else return rcp32(x);
+}
 
 // Targets of Eq. (13constraints) divided by rho:
 // [1, u, u_a u_b + T delta_ab (xx,yy,zz,xy,xz,yz), u_a (u^2 + (D+2) T)].
@@ -173,7 +201,7 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
     });
     ok = ok && (dj > T(0));
     J[tri(j, j)] = dj;
-    rd[j] = T(1) / dj;
+    rd[j] = recip(dj);
     static_for<j + 1, NM>([&](auto II) {
       constexpr int i = decltype(II)::value;
       T a = J[tri(i, j)];
@@ -316,20 +344,31 @@ __device__ __forceinline__ void gaussian_guess(double ux, double uy, double uz, 
   for (int k = 0; k < NM; ++k) lam[k] = l[k];
 }
 
-// alpha(eps) of Eq. (alpha).
-__device__ __forceinline__ double alpha_of(double eps, double tau) {
-  return eps < 1e-2 ? 1.0 : eps < 1e-1 ? 1.05 : eps < 1.0 ? 1.35 : 1.0 / tau;
-}
+// Branch of alpha(eps) in Eq. (alpha): eps < 1e-2, < 1e-1, < 1, >= 1 (Phys::omega).
 __device__ __forceinline__ int alpha_branch(double eps) {
   return eps < 1e-2 ? 0 : eps < 1e-1 ? 1 : eps < 1.0 ? 2 : 3;
 }
 
-// True if an FP32 estimate s39 of 39*eps with absolute error below 2.5e-5
-// could lie on the other side of a threshold of Eq. (alpha) than the FP64 value.
-__device__ __forceinline__ bool near_threshold(float s39) {
-  constexpr float band = 5e-5f;
-  return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band ||
-         !(s39 == s39);
+// 1 / tau_eff of that branch (selects, so the table is not indexed at run time).
+__device__ __forceinline__ double omega_of(const Phys& ph, int branch) {
+  return branch == 0 ? ph.omega[0] : branch == 1 ? ph.omega[1] : branch == 2 ? ph.omega[2]
+                                                                            : ph.omega[3];
+}
+
+// FP32 screen of s = 39 eps = sum_i |f_i - f^eq_i| / f^eq_i (Eq. DeltaAvg).  With
+// u = 2^-24: each float view (f~, F~, rho~) is within 2u of its double, q = rho~ F~
+// adds u, the difference u, rcp32 2u and the product u, so each term is within
+// 7u + 11u t of t (using |f| / f^eq <= 1 + t); four interleaved partial sums of at
+// most 10 terms add at most 11u s.  In all |s32 - s| <= u (273 + 22 s), i.e.
+// 1.63e-5 + 1.31e-6 s, provided every view and q are normal floats: F~_i, |f~_i|
+// >= 2^-100 and rho~ in [2^-20, 2^20].  True when that fails, when s32 is not
+// finite, or when s32 lies within 3e-5 + 3e-6 s32 (about twice the bound) of a
+// threshold 39 * {1e-2, 1e-1, 1}: then the FP64 value decides the branch.
+__device__ __forceinline__ bool screen_undecided(float s39, float lo, float rho32) {
+  if (!(s39 < 1e30f) || !(lo >= 0x1p-100f) || !(rho32 >= 0x1p-20f && rho32 <= 0x1p20f))
+    return true;
+  const float band = 3e-5f + 3e-6f * s39;
+  return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;
 }
 
 struct CellStats {
@@ -346,7 +385,7 @@ struct Macro {
 
 __device__ __forceinline__ Macro macro_from_moments(double rho, double jx, double jy, double jz,
                                                     double e2, double inv_2cv) {
-  const double ir = 1.0 / rho;
+  const double ir = rcp64(rho);
   Macro M;
   M.rho = rho;
   M.ux = jx * ir; M.uy = jy * ir; M.uz = jz * ir;

@@ -195,16 +195,20 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
   if constexpr (sizeof(P) == 8) {
     P f[Q];
     gather<ODD, P>(d, cell, nb, 0, f);
-    // FP32 estimate of 39 eps from float views (absolute error < 2.5e-5),
-    // FP64 value when that cannot decide the branch of Eq. (alpha)
-    float s32 = 0.0f;
+    // FP32 screen of 39 eps from float views (error bound: screen_undecided);
+    // the FP64 value where the screen cannot decide the branch of Eq. (alpha)
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float lo = 1.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float feq = rho32 * trunc_float(F[i]);
-      s32 += fabsf(trunc_float(f[i]) - feq) / feq;
+      const float Fi = trunc_float(F[i]), fi = trunc_float(f[i]);
+      const float feq = rho32 * Fi;
+      acc[i & 3] += fabsf(fi - feq) * rcp32(feq);
+      lo = fminf(lo, fminf(Fi, fabsf(fi)));
     }
+    const float s32 = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     eps = (double)s32 * (1.0 / Q);
-    if (near_threshold(s32)) {
+    if (screen_undecided(s32, lo, rho32)) {
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -213,8 +217,7 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
       }
       eps = s * (1.0 / Q);
     }
-    const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
-    const double omega = 1.0 / (ph.tau * alpha);
+    const double omega = omega_of(ph, alpha_branch(eps));
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       push<ODD, P, i>(d, cell, nb, 0, fma(-omega, fma(-rho, F[i], f[i]), f[i]));
@@ -231,16 +234,15 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     const double* __restrict__ href = d.href;
     P f[Q];
     gather<ODD, P>(d, cell, nb, 0, f);
-    float s32 = 0.0f;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double Fi = F[i];
       f[i] -= round_float(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
-      s32 += fabsf(f[i]) / (rho32 * trunc_float(Fi));
+      acc[i & 3] += fabsf(f[i]) * rcp32(rho32 * trunc_float(Fi));
     }
-    eps = (double)s32 * (1.0 / Q);
-    const double alpha = ph.kn_sensor ? alpha_of(eps, ph.tau) : 1.0;
-    const float omega = (float)(1.0 / (ph.tau * alpha));
+    eps = (double)((acc[0] + acc[1]) + (acc[2] + acc[3])) * (1.0 / Q);
+    const float omega = (float)omega_of(ph, alpha_branch(eps));
     P f2[Q];
     gather<ODD, P>(d, cell, nb, 0, f2);  // the stored values again (cached)
     static_for<0, Q>([&](auto I) {
@@ -630,6 +632,18 @@ __global__ void k_batch_advance(BatchEntry* E, int nlat, int n) {
 }
 
 // Library exponential and CUDA's exp side by side (diagnostic).
+__global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y32, float* ref32,
+                               long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    y[i] = rcp64(x[i]);
+    ref[i] = 1.0 / x[i];
+    const float xf = (float)x[i];
+    y32[i] = rcp32(xf);
+    ref32[i] = 1.0f / xf;
+  }
+}
+
 __global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
   load_exp_table();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;

@@ -280,6 +280,10 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   d.ph.maxit = p->newton_maxit;
   d.ph.min_upd = p->newton_min_upd;
   d.ph.kn_sensor = p->kn_sensor ? 1 : 0;
+  {
+    const double alpha[4] = {1.0, 1.05, 1.35, 1.0 / p->tau};  // Eq. (alpha)
+    for (int b = 0; b < 4; ++b) d.ph.omega[b] = 1.0 / (p->tau * (p->kn_sensor ? alpha[b] : 1.0));
+  }
   int rc = LBM39_OK;
   // reference populations of the precision form and their moments
   double href[2 * Q] = {0}, heq[2 * Q] = {0};
@@ -538,6 +542,16 @@ int lbm39_selftest_exp(const double* x, double* y, double* ref, int64_t n, void*
   if (n == 0) return LBM39_OK;
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
   k_selftest_exp<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, y, ref, n);
+  return last_launch();
+}
+
+int lbm39_selftest_rcp(const double* x, double* y, double* ref, float* y32, float* ref32,
+                       int64_t n, void* cuda_stream) {
+  if (!x || !y || !ref || !y32 || !ref32 || n < 0) return LBM39_ERR_ARG;
+  if (n == 0) return LBM39_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+  k_selftest_rcp<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, y, ref, y32, ref32,
+                                                                          n);
   return last_launch();
 }
 
