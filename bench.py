@@ -399,7 +399,7 @@ def main():
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory()
         h_rho, h_u, h_T = pin(s.rho), pin(s.u), pin(s.T)
         h_out = torch.empty((6, N), dtype=torch.float64).pin_memory()
-        ke = max(4, args.steps // 4)
+        ke = args.steps
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()

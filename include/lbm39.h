@@ -135,8 +135,10 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
  * (see lbm39_sync). */
 int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const double* T);
 
-/* As lbm39_init with host arrays: copies them to the device (staging inside
- * the auxiliary buffer) on the lattice's stream and waits for the copies. */
+/* As lbm39_init with host arrays, and waits until the initial state is
+ * formed.  Page-locked arrays (cudaHostAlloc, cudaHostRegister, pinned torch
+ * tensors; each array one allocation) are read by the init kernel directly;
+ * pageable ones are copied through the staging area of the auxiliary buffer. */
 int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const double* T);
 
 /* Enqueues nsteps >= 0 time steps (Sec. 3: per fluid cell, macroscopic
@@ -157,8 +159,9 @@ int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells);
  * may be NULL.  Non-fluid cells read 0. */
 int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p);
 
-/* As lbm39_read into host arrays (staged through the auxiliary buffer);
- * returns when the copies are done. */
+/* As lbm39_read into host arrays; returns when they are written.  Page-locked
+ * arrays (each one allocation) are written by the read-out kernel directly;
+ * pageable ones through the staging area of the auxiliary buffer. */
 int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double* p);
 
 /* Waits for the stream and fills *s (counters and conserved sums). */

@@ -323,6 +323,28 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   return LBM39_OK;
 }
 
+// Device address of a host array of `bytes` bytes that kernels may access
+// directly -- page-locked and mapped (cudaHostAlloc, cudaHostRegister, pinned
+// torch tensors), its first and last byte in one contiguous mapping -- else
+// nullptr (pageable memory goes through the staging area).
+static void* mapped_host(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  const char* last = static_cast<const char*>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+      cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer ||
+      !b.devicePointer)
+    return nullptr;
+  if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) !=
+      (ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
+
 static int init_range(lbm39_lattice* L, const double* rho, const double* u, long long us,
                       const double* T, long long c0, long long len) {
   if (L->mixed) Launch<float>::init(L, rho, u, us, T, c0, len);
@@ -349,6 +371,17 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
   if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
   int rc = init_begin(L);
   if (rc) return rc;
+  const size_t nb = sizeof(double) * L->N;
+  const void* drho = mapped_host(rho, nb);
+  const void* du = mapped_host(u, 3 * nb);
+  const void* dT = mapped_host(T, nb);
+  if (drho && du && dT) {  // page-locked: the init kernel reads them directly
+    rc = init_range(L, static_cast<const double*>(drho), static_cast<const double*>(du), L->N,
+                    static_cast<const double*>(dT), 0, L->N);
+    if (rc) return rc;
+    CUDA_OK(cudaStreamSynchronize(L->stream));
+    return LBM39_OK;
+  }
   const long long C = std::min(L->N, STAGE_CELLS);
   double* s = L->stage();
   for (long long c0 = 0; c0 < L->N; c0 += C) {
@@ -421,6 +454,19 @@ int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
 int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
   if (!L) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
+  const size_t nb = sizeof(double) * L->N;
+  void* drho = rho ? mapped_host(rho, nb) : nullptr;
+  void* du = u ? mapped_host(u, 3 * nb) : nullptr;
+  void* dT = T ? mapped_host(T, nb) : nullptr;
+  void* dp = p ? mapped_host(p, nb) : nullptr;
+  if ((!rho || drho) && (!u || du) && (!T || dT) && (!p || dp)) {
+    // page-locked: the read-out kernel writes them directly
+    const int rc = read_range(L, static_cast<double*>(drho), static_cast<double*>(du), L->N,
+                              static_cast<double*>(dT), static_cast<double*>(dp), 0, L->N);
+    if (rc) return rc;
+    CUDA_OK(cudaStreamSynchronize(L->stream));
+    return LBM39_OK;
+  }
   const long long C = std::min(L->N, STAGE_CELLS);
   double* s = L->stage();
   for (long long c0 = 0; c0 < L->N; c0 += C) {
