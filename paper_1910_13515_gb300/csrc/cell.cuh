@@ -101,6 +101,19 @@ __device__ __forceinline__ float trunc_float(double x) {
   return e > 0 ? __uint_as_float(bits) : 0.0f;
 }
 
+// The same view in three integer operations for a double whose exponent E
+// (biased, 11 bits) gives a normal float (897 <= E <= 1150; callers check E
+// with exp_field): the funnel shift leaves E mod 512 above the top 23
+// mantissa bits, and subtracting 384 in that 9-bit field leaves E - 896.
+__device__ __forceinline__ float view_float(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned m = __funnelshift_l(lo, hi, 3);
+  return __uint_as_float((m - (384u << 23)) | (hi & 0x80000000u));
+}
+
+// Biased exponent field of a double (bits 52..62 in place, as an int).
+__device__ __forceinline__ int exp_field(double x) { return __double2hiint(x) & 0x7ff00000; }
+
 // Exact float -> double by integer operations (normal floats and zero; other
 // values take the conversion instruction).
 __device__ __forceinline__ double exact_double(float v) {
@@ -360,12 +373,16 @@ __device__ __forceinline__ double omega_of(const Phys& ph, int branch) {
 // adds u, the difference u, rcp32 2u and the product u, so each term is within
 // 7u + 11u t of t (using |f| / f^eq <= 1 + t); four interleaved partial sums of at
 // most 10 terms add at most 11u s.  In all |s32 - s| <= u (273 + 22 s), i.e.
-// 1.63e-5 + 1.31e-6 s, provided every view and q are normal floats: F~_i, |f~_i|
-// >= 2^-100 and rho~ in [2^-20, 2^20].  True when that fails, when s32 is not
-// finite, or when s32 lies within 3e-5 + 3e-6 s32 (about twice the bound) of a
-// threshold 39 * {1e-2, 1e-1, 1}: then the FP64 value decides the branch.
-__device__ __forceinline__ bool screen_undecided(float s39, float lo, float rho32) {
-  if (!(s39 < 1e30f) || !(lo >= 0x1p-100f) || !(rho32 >= 0x1p-20f && rho32 <= 0x1p20f))
+// 1.63e-5 + 1.31e-6 s, provided every view and q are normal floats: F_i, |f_i| in
+// [2^-100, 2^100] (exponent fields within SCREEN_EMIN..SCREEN_EMAX) and rho~ in
+// [2^-20, 2^20].  True when that fails, when s32 is not finite, or when s32 lies
+// within 3e-5 + 3e-6 s32 (about twice the bound) of a threshold 39 * {1e-2, 1e-1, 1}:
+// then the FP64 value decides the branch.
+constexpr int SCREEN_EMIN = (1023 - 100) << 20, SCREEN_EMAX = (1023 + 100) << 20;
+
+__device__ __forceinline__ bool screen_undecided(float s39, int emin, int emax, float rho32) {
+  if (!(s39 < 1e30f) || emin < SCREEN_EMIN || emax > SCREEN_EMAX ||
+      !(rho32 >= 0x1p-20f && rho32 <= 0x1p20f))
     return true;
   const float band = 3e-5f + 3e-6f * s39;
   return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;

@@ -198,17 +198,19 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     // FP32 screen of 39 eps from float views (error bound: screen_undecided);
     // the FP64 value where the screen cannot decide the branch of Eq. (alpha)
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float lo = 1.0f;
+    int emin = SCREEN_EMAX, emax = SCREEN_EMIN;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float Fi = trunc_float(F[i]), fi = trunc_float(f[i]);
-      const float feq = rho32 * Fi;
-      acc[i & 3] += fabsf(fi - feq) * rcp32(feq);
-      lo = fminf(lo, fminf(Fi, fabsf(fi)));
+      const double Fd = F[i];
+      const int eF = exp_field(Fd), ef = exp_field(f[i]);
+      emin = min(emin, min(eF, ef));
+      emax = max(emax, max(eF, ef));
+      const float feq = rho32 * view_float(Fd);
+      acc[i & 3] += fabsf(view_float(f[i]) - feq) * rcp32(feq);
     }
     const float s32 = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     eps = (double)s32 * (1.0 / Q);
-    if (screen_undecided(s32, lo, rho32)) {
+    if (screen_undecided(s32, emin, emax, rho32)) {
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
