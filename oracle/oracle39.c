@@ -201,35 +201,38 @@ void o39_jacobian(const double *lam, double *J) {
   jacobian_from_F(F, J);
 }
 
-/* "Compute inverse of J" (Sec. 5 step table): textbook Gauss-Jordan
+/* Inverse of the n x n matrix Jin (n <= NM) by textbook Gauss-Jordan
  * elimination with partial pivoting.  Returns 0, or -1 if singular. */
-int o39_invert(const double *Jin, double *Jinv) {
+static int invert_n(const double *Jin, double *Jinv, int n) {
   double a[NM][2 * NM];
-  for (int r = 0; r < NM; ++r)
-    for (int c = 0; c < NM; ++c) {
-      a[r][c] = Jin[r * NM + c];
-      a[r][NM + c] = (r == c) ? 1.0 : 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      a[r][c] = Jin[r * n + c];
+      a[r][n + c] = (r == c) ? 1.0 : 0.0;
     }
-  for (int c = 0; c < NM; ++c) {
+  for (int c = 0; c < n; ++c) {
     int p = c;
-    for (int r = c + 1; r < NM; ++r)
+    for (int r = c + 1; r < n; ++r)
       if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
     if (!(fabs(a[p][c]) > 0.0)) return -1;
     if (p != c)
-      for (int k = 0; k < 2 * NM; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+      for (int k = 0; k < 2 * n; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
     double piv = a[c][c];
-    for (int k = 0; k < 2 * NM; ++k) a[c][k] /= piv;
-    for (int r = 0; r < NM; ++r) {
+    for (int k = 0; k < 2 * n; ++k) a[c][k] /= piv;
+    for (int r = 0; r < n; ++r) {
       if (r == c) continue;
       double fct = a[r][c];
       if (fct == 0.0) continue;
-      for (int k = 0; k < 2 * NM; ++k) a[r][k] -= fct * a[c][k];
+      for (int k = 0; k < 2 * n; ++k) a[r][k] -= fct * a[c][k];
     }
   }
-  for (int r = 0; r < NM; ++r)
-    for (int c = 0; c < NM; ++c) Jinv[r * NM + c] = a[r][NM + c];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Jinv[r * n + c] = a[r][n + c];
   return 0;
 }
+
+/* "Compute inverse of J" (Sec. 5 step table). */
+int o39_invert(const double *Jin, double *Jinv) { return invert_n(Jin, Jinv, NM); }
 
 static double maxabs(const double *v) {
   double r = 0.0;
@@ -263,6 +266,9 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
 }
 
 #define LS_MAX 30
+#define N5 5               /* constraints of the fallback equilibrium */
+#define FALLBACK_MAXIT 50  /* Newton updates of the fallback from its Gaussian start */
+#define FALLBACK_TOL 1e-12
 
 /* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
@@ -326,6 +332,150 @@ int o39_newton(const double *m, double *lam, double tol, int maxit, int min_upd,
   return status;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Fallback where the 13-moment equilibrium does not exist.
+ * reading (the paper does not say what a cell does when its constraint solve
+ * fails): outside the moment cone of the 39 velocities no positive
+ * distribution has the 13 target moments, and Newton cannot converge.  Such a
+ * cell relaxes instead to the maximum-entropy equilibrium under the five
+ * collision invariants phi5 = [1, xi, |xi|^2] only,
+ *   F_i = exp(mu_0 + mu . xi_i + mu_4 |xi_i|^2),  sum_i F_i phi5(xi_i) = [1, u, u^2 + D T],
+ * which exists far beyond that cone and conserves mass, momentum and energy
+ * (with g^eq = (2 C_v - D) T f^eq as for the full equilibrium).  It is solved
+ * from the Gaussian start by the same damped Newton iteration; the cell's 13
+ * multipliers keep their last accepted value, so the next step tries the full
+ * solve again. */
+
+static void basis5_i(int i, double *phi) {
+  phi[0] = 1.0;
+  phi[1] = VEL[i][0]; phi[2] = VEL[i][1]; phi[3] = VEL[i][2];
+  phi[4] = VEL[i][0] * VEL[i][0] + VEL[i][1] * VEL[i][1] + VEL[i][2] * VEL[i][2];
+}
+
+void o39_targets5(const double *u, double T, double *m) {
+  m[0] = 1.0;
+  m[1] = u[0]; m[2] = u[1]; m[3] = u[2];
+  m[4] = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + DIM * T;
+}
+
+void o39_feq5(const double *mu, double *F) {
+  build_lattice();
+  for (int i = 0; i < Q; ++i) {
+    double phi[N5];
+    basis5_i(i, phi);
+    double e = 0.0;
+    for (int k = 0; k < N5; ++k) e += mu[k] * phi[k];
+    F[i] = exp(e);
+  }
+}
+
+static void residual5(const double *F, const double *m, double *G) {
+  for (int k = 0; k < N5; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      double phi[N5];
+      basis5_i(i, phi);
+      s += F[i] * phi[k];
+    }
+    G[k] = s - m[k];
+  }
+}
+
+static double maxabs_n(const double *v, int n) {
+  double r = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double a = fabs(v[k]);
+    if (!(a <= r)) r = a;
+  }
+  return r;
+}
+
+static double sumsq_n(const double *v, int n) {
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += v[k] * v[k];
+  return s;
+}
+
+/* Gaussian start: mu = (., u/T, -1/(2T)), mu_0 normalising sum_i F_i = 1. */
+void o39_gaussian_guess5(const double *u, double T, double *mu) {
+  build_lattice();
+  mu[0] = 0.0;
+  mu[1] = u[0] / T; mu[2] = u[1] / T; mu[3] = u[2] / T;
+  mu[4] = -0.5 / T;
+  double F[Q];
+  o39_feq5(mu, F);
+  double s = 0.0;
+  for (int i = 0; i < Q; ++i) s += F[i];
+  mu[0] = -log(s);
+}
+
+/* Newton for the five multipliers with the same stopping rule, polishing step
+ * and backtracking as o39_newton.  Returns 0 or 1 (failure). */
+int o39_newton5(const double *m, double *mu, double tol, int maxit, int *n_upd_out, double *F) {
+  build_lattice();
+  double G[N5];
+  o39_feq5(mu, F);
+  residual5(F, m, G);
+  int n_upd = 0, status = 0, polished = 0;
+  for (;;) {
+    double r = maxabs_n(G, N5);
+    if (r < tol && (r < 1e-2 * tol || polished)) break;
+    if (n_upd >= maxit) { status = 1; break; }
+    double J[N5 * N5], Ji[N5 * N5], d[N5];
+    for (int k = 0; k < N5; ++k)
+      for (int l = 0; l < N5; ++l) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) {
+          double phi[N5];
+          basis5_i(i, phi);
+          s += F[i] * phi[k] * phi[l];
+        }
+        J[k * N5 + l] = s;
+      }
+    if (invert_n(J, Ji, N5) != 0) { status = 1; break; }
+    for (int k = 0; k < N5; ++k) {
+      double s = 0.0;
+      for (int l = 0; l < N5; ++l) s += Ji[k * N5 + l] * G[l];
+      d[k] = s;
+    }
+    double mt[N5], Ft[Q], Gt[N5];
+    polished = (r < tol);
+    if (polished) {
+      for (int k = 0; k < N5; ++k) mt[k] = mu[k] - d[k];
+      o39_feq5(mt, Ft);
+      residual5(Ft, m, Gt);
+    } else {
+      double s0 = sumsq_n(G, N5), t = 1.0;
+      int ok = 0;
+      for (int ls = 0; ls <= LS_MAX; ++ls) {
+        for (int k = 0; k < N5; ++k) mt[k] = mu[k] - t * d[k];
+        o39_feq5(mt, Ft);
+        residual5(Ft, m, Gt);
+        if (sumsq_n(Gt, N5) < s0) { ok = 1; break; }
+        t *= 0.5;
+      }
+      if (!ok) { status = 1; break; }
+    }
+    memcpy(mu, mt, sizeof mt);
+    memcpy(F, Ft, sizeof Ft);
+    memcpy(G, Gt, sizeof Gt);
+    ++n_upd;
+  }
+  if (n_upd_out) *n_upd_out = n_upd;
+  return status;
+}
+
+/* The fallback equilibrium F of the state (u, T) into F if its solve
+ * converges (F unchanged otherwise).  Returns the fallback's status. */
+static int fallback_equilibrium(const double *u, double T, double *F) {
+  double m5[N5], mu[N5], F5[Q];
+  o39_targets5(u, T, m5);
+  o39_gaussian_guess5(u, T, mu);
+  if (o39_newton5(m5, mu, FALLBACK_TOL, FALLBACK_MAXIT, NULL, F5) != 0) return 1;
+  memcpy(F, F5, sizeof F5);
+  return 0;
+}
+
 /* alpha(eps), Eq. (alpha): 1 below 1e-2, 1.05 on [1e-2,1e-1), 1.35 on
  * [1e-1,1), and 1/tau from 1 upward (then tau*alpha = 1: h* = h^eq). */
 double o39_alpha(double eps, double tau) {
@@ -379,6 +529,7 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam,
   double m[NM], F[Q];
   o39_targets(u, T, m);
   int st = o39_newton(m, lam, p->newton_tol, p->newton_maxit, p->newton_min_upd, n_upd, F);
+  if (st) fallback_equilibrium(u, T, F);
   double feq[Q], geq[Q];
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
@@ -409,6 +560,7 @@ int o39_equilibrium(const o39_params *p, double rho, const double *u, double T,
   o39_gaussian_guess(u, T, lam);
   int nu = 0;
   int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, &nu, F);
+  if (st) fallback_equilibrium(u, T, F);
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
     geq[i] = (2.0 * cv - DIM) * T * feq[i];

@@ -89,6 +89,12 @@ def lib():
         _lib.o39_alpha.argtypes = [d, d]
         _lib.o39_alpha.restype = d
         _lib.o39_cell_macros.argtypes = [P, vp, vp, vp, vp, vp]
+        _lib.o39_newton5.argtypes = [vp, vp, d, ctypes.c_int, vp, vp]
+        _lib.o39_newton5.restype = ctypes.c_int
+        _lib.o39_targets5.argtypes = [vp, d, vp]
+        _lib.o39_targets5.restype = None
+        _lib.o39_gaussian_guess5.argtypes = [vp, d, vp]
+        _lib.o39_gaussian_guess5.restype = None
         _lib.o39_collide_cell.argtypes = [P, vp, vp, vp, vp, vp, vp]
         _lib.o39_collide_cell.restype = ctypes.c_int
         _lib.o39_equilibrium.argtypes = [P, d, vp, d, vp, vp, vp, ctypes.c_int]
@@ -179,6 +185,24 @@ def newton(m, lam0, tol=1e-12, maxit=30, min_upd=0):
     st = lib().o39_newton(_p(_f64(m)), _p(lam), float(tol), int(maxit), int(min_upd),
                           ctypes.byref(nu), _p(F))
     return lam, F, nu.value, st
+
+
+def targets5(u, T) -> np.ndarray:
+    out = np.zeros(5)
+    lib().o39_targets5(_p(_f64(u)), float(T), _p(out))
+    return out
+
+
+def newton5(u, T, tol=1e-12, maxit=50):
+    """Fallback equilibrium of (u, T) (five collision invariants) from the Gaussian start:
+    (mu, F, n_updates, status)."""
+    m = targets5(u, T)
+    mu = np.zeros(5)
+    lib().o39_gaussian_guess5(_p(_f64(u)), float(T), _p(mu))
+    F = np.zeros(Q)
+    nu = ctypes.c_int(0)
+    st = lib().o39_newton5(_p(m), _p(mu), float(tol), int(maxit), ctypes.byref(nu), _p(F))
+    return mu, F, nu.value, st
 
 
 def alpha(eps, tau) -> float:
@@ -273,8 +297,10 @@ class State:
     stats: Stats = field(default_factory=Stats)
 
 
-def init(cfg: Config, mask, rho, u, T) -> State:
-    """Equilibrium initial state.  rho, T: (N,), u: (3, N) (x fastest in cell index)."""
+def init(cfg: Config, mask, rho, u, T, allow_failed: bool = False) -> State:
+    """Equilibrium initial state.  rho, T: (N,), u: (3, N) (x fastest in cell index).
+    Cells whose 13-moment solve fails take the fallback equilibrium; that raises unless
+    allow_failed (then State.init_failed counts them)."""
     N = cfg.ncells
     mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(N)
     rho = _f64(rho).reshape(N)
@@ -286,9 +312,11 @@ def init(cfg: Config, mask, rho, u, T) -> State:
     p = cfg.params()
     failed = lib().o39_init(ctypes.byref(p), _p(mask), _p(rho), _p(u), _p(T), _p(f), _p(g),
                             _p(lam), int(cfg.init_maxit))
-    if failed:
+    if failed and not allow_failed:
         raise RuntimeError(f"oracle init: {failed} cells failed the Newton solve")
-    return State(cfg, mask, f, g, lam)
+    st = State(cfg, mask, f, g, lam)
+    st.init_failed = int(failed)
+    return st
 
 
 def step(st: State, nsteps: int) -> int:

@@ -336,6 +336,155 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
   return NewtonResult{n, failed};
 }
 
+// ---------------------------------------------------------------------------
+// Fallback where the 13-moment equilibrium does not exist (reading: the paper
+// does not say what a cell does when its constraint solve fails).  Outside the
+// moment cone of the 39 velocities no positive distribution has the 13 target
+// moments, and Newton cannot converge.  Such a cell relaxes instead to the
+// maximum-entropy equilibrium under the five collision invariants [1, xi,
+// |xi|^2] only, F_i = exp(mu_0 + mu.xi_i + mu_4 |xi_i|^2) with
+// sum_i F_i [1, xi_i, |xi_i|^2] = [1, u, u^2 + D T]: it exists far beyond that
+// cone and conserves mass, momentum and energy (g^eq = (2 C_v - D) T f^eq as
+// for the full equilibrium).  Same damped Newton iteration and stopping rule
+// as the full solve, from the Gaussian start.  Rare, so written for size: a
+// rolled loop over the velocities and a non-inlined function.
+constexpr int N5 = 5;
+constexpr int FALLBACK_MAXIT = 50;
+constexpr double FALLBACK_TOL = 1e-12;
+
+// F = exp(phi5 . (mu - t dl)) (t = 0: mu itself) and G = sum_i F_i phi5(xi_i) - m5.
+template <int BLK>
+__device__ __forceinline__ void eval5(WS<BLK> mu, WS<BLK> dl, double t, WS<BLK> F,
+                                      const double (&m5)[N5], double (&G)[N5]) {
+  double l[N5];
+#pragma unroll
+  for (int k = 0; k < N5; ++k) l[k] = t == 0.0 ? mu[k] : fma(-t, dl[k], mu[k]);
+  double s[N5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+  for (int i = 0; i < Q; ++i) {
+    const double cx = kCX[i], cy = kCY[i], cz = kCZ[i];
+    const double c2 = cx * cx + cy * cy + cz * cz;
+    const double Fi = exp_tang(l[0] + l[1] * cx + l[2] * cy + l[3] * cz + l[4] * c2);
+    F[i] = Fi;
+    s[0] += Fi;
+    s[1] = fma(Fi, cx, s[1]);
+    s[2] = fma(Fi, cy, s[2]);
+    s[3] = fma(Fi, cz, s[3]);
+    s[4] = fma(Fi, c2, s[4]);
+  }
+#pragma unroll
+  for (int k = 0; k < N5; ++k) G[k] = s[k] - m5[k];
+}
+
+// Newton direction of the fallback: J = sum_i F_i phi5 phi5^T (symmetric
+// positive definite), J d = b by elimination without pivoting; false if a
+// pivot is not positive.
+template <int BLK>
+__device__ __forceinline__ bool direction5(WS<BLK> F, double (&b)[N5]) {
+  double A[N5][N5];
+#pragma unroll
+  for (int k = 0; k < N5; ++k)
+#pragma unroll
+    for (int l = 0; l < N5; ++l) A[k][l] = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < Q; ++i) {
+    const double cx = kCX[i], cy = kCY[i], cz = kCZ[i];
+    const double p[N5] = {1.0, cx, cy, cz, cx * cx + cy * cy + cz * cz};
+    const double Fi = F[i];
+#pragma unroll
+    for (int k = 0; k < N5; ++k)
+#pragma unroll
+      for (int l = 0; l <= k; ++l) A[k][l] = fma(Fi * p[k], p[l], A[k][l]);
+  }
+#pragma unroll
+  for (int k = 0; k < N5; ++k)
+#pragma unroll
+    for (int l = k + 1; l < N5; ++l) A[k][l] = A[l][k];
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < N5; ++c) {
+    ok = ok && (A[c][c] > 0.0);
+    const double ip = 1.0 / A[c][c];
+#pragma unroll
+    for (int r = c + 1; r < N5; ++r) {
+      const double f = A[r][c] * ip;
+#pragma unroll
+      for (int k = c; k < N5; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+      b[r] = fma(-f, b[c], b[r]);
+    }
+  }
+#pragma unroll
+  for (int r = N5 - 1; r >= 0; --r) {
+    double a = b[r];
+#pragma unroll
+    for (int k = r + 1; k < N5; ++k) a = fma(-A[r][k], b[k], a);
+    b[r] = a / A[r][r];
+  }
+  return ok;
+}
+
+// The fallback equilibrium into F for the cell whose 13 normalised targets
+// are in the workspace (m: their u and second moments give the five targets);
+// overwrites the m and dl slots.  Returns 1 if its solve fails too (F then
+// holds a partial iterate and must be restored by the caller).
+template <int BLK>
+__device__ __noinline__ int fallback_equilibrium(WS<BLK> w, double T) {
+  WS<BLK> F = w.at(WS_E), mu = w.at(WS_M), dl = w.at(WS_DL);
+  const double m5[N5] = {1.0, mu[1], mu[2], mu[3], mu[4] + mu[5] + mu[6]};
+  const double it = 1.0 / T;
+  mu[0] = 0.0;
+  mu[1] = m5[1] * it; mu[2] = m5[2] * it; mu[3] = m5[3] * it;
+  mu[4] = -0.5 * it;
+  double G[N5];
+  eval5<BLK>(mu, dl, 0.0, F, m5, G);
+  {
+    double s = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) s += F[i];
+    mu[0] = -log(s);
+  }
+  eval5<BLK>(mu, dl, 0.0, F, m5, G);
+  int n = 0, ls = 0;
+  bool polished = false, first = true;
+  double t = 0.0, s0 = 0.0;
+  for (;;) {
+    if (!first) {
+      eval5<BLK>(mu, dl, t, F, m5, G);
+      double ss = 0.0;
+#pragma unroll
+      for (int k = 0; k < N5; ++k) ss = fma(G[k], G[k], ss);
+      if (!polished && !(ss < s0)) {  // reject: halve the step
+        if (++ls > LS_MAX) return 1;
+        t *= 0.5;
+        continue;
+      }
+#pragma unroll
+      for (int k = 0; k < N5; ++k) mu[k] = fma(-t, dl[k], mu[k]);
+      ++n;
+    }
+    first = false;
+    double r = 0.0, ss = 0.0;
+#pragma unroll
+    for (int k = 0; k < N5; ++k) {
+      const double a = fabs(G[k]);
+      r = (a <= r) ? r : a;
+      ss = fma(G[k], G[k], ss);
+    }
+    if (r < FALLBACK_TOL && (r < 1e-2 * FALLBACK_TOL || polished)) return 0;
+    if (n >= FALLBACK_MAXIT) return 1;
+    s0 = ss;
+    double b[N5];
+#pragma unroll
+    for (int k = 0; k < N5; ++k) b[k] = G[k];
+    if (!direction5<BLK>(F, b)) return 1;
+#pragma unroll
+    for (int k = 0; k < N5; ++k) dl[k] = b[k];
+    polished = r < FALLBACK_TOL;
+    t = 1.0;
+    ls = 0;
+  }
+}
+
 // Gaussian cold start (reading): lam_1 = u/T, diagonal lam_2 = -1/(2T), the rest 0,
 // lam_0 normalising sum_i F_i = 1.
 template <int BLK>

@@ -291,6 +291,17 @@ __device__ __forceinline__ void store_solver_state(const Desc& d, long long cell
   for (int i = 0; i < Q; ++i) st[(NM + i) * d.Np + cell] = w[WS_E + i];
 }
 
+// Where the 13-moment solve failed: the fallback equilibrium into F, or, if
+// that fails too, F back at the stored multipliers (the last accepted ones).
+template <int BLK>
+__device__ __forceinline__ void fallback_or_restore(const Desc& d, long long cell, WS<BLK> w,
+                                                    double T) {
+  if (fallback_equilibrium<BLK>(w, T)) {
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) w[WS_E + i] = d.lam[(NM + i) * d.Np + cell];
+  }
+}
+
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 template <bool ODD, class P, int BLK>
@@ -304,6 +315,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   load_solver_state<BLK>(d, cell, w);
   const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit, true);
   store_solver_state<BLK>(d, cell, w);
+  if (nr.failed) fallback_or_restore<BLK>(d, cell, w, M.T);
   const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, c), M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
@@ -354,12 +366,13 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
       targets<BLK>(ux, uy, uz, TT, m);
       gaussian_guess<BLK>(ux, uy, uz, TT, lam);
       const NewtonResult nr = newton<BLK, false>(w, d.ph, maxit, false);
+      store_solver_state<BLK>(d, cell, w);
+      if (nr.failed) fallback_or_restore<BLK>(d, cell, w, TT);
       const double cgr = d.ph.cg * TT * rr;
       for (int i = 0; i < Q; ++i) {
         pop[(long long)i * d.Np + cell] = to_store<P>(d, i, rr * F[i]);
         pop[(long long)(Q + i) * d.Np + cell] = to_store<P>(d, Q + i, cgr * F[i]);
       }
-      store_solver_state<BLK>(d, cell, w);
       atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
     } else {
       for (int j = 0; j < 2 * Q; ++j) pop[(long long)j * d.Np + cell] = P(0);

@@ -1,0 +1,81 @@
+"""Pins of the oracle's fallback equilibrium: where the 13-moment equilibrium does not exist
+(outside the moment cone of the 39 velocities), a cell relaxes to the maximum-entropy
+equilibrium under the five collision invariants [1, xi, |xi|^2] (a reading; the paper does not
+say what a cell does when its constraint solve fails)."""
+import numpy as np
+from scipy.optimize import linprog
+
+RNG = np.random.default_rng(17)
+# states found outside the cone: behind a NACA0012 at Ma 1.5 (T_inf = 0.5) and in the
+# rms-Ma-0.8 box
+OUTSIDE = [((1.416, -0.348, 0.0), 0.414), ((-0.401, 0.936, -0.488), 0.397)]
+
+
+def _invariants(vel, F):
+    v = vel.astype(float)
+    return np.array([F.sum(), F @ v[:, 0], F @ v[:, 1], F @ v[:, 2], F @ (v ** 2).sum(1)])
+
+
+def _in_cone(oracle, u, T):
+    """True if some strictly positive weights on the 39 velocities have the 13 target moments
+    (linear programme: maximise the smallest weight)."""
+    vel, _, _ = oracle.lattice()
+    Phi = np.array([oracle.basis(v) for v in np.asarray(vel, np.int32)])
+    m = oracle.targets(np.asarray(u, float), T)
+    A_eq = np.hstack([Phi.T, np.zeros((13, 1))])
+    A_ub = np.hstack([-np.eye(39), np.ones((39, 1))])
+    res = linprog(np.r_[np.zeros(39), -1.0], A_ub=A_ub, b_ub=np.zeros(39), A_eq=A_eq, b_eq=m,
+                  bounds=[(0, None)] * 39 + [(None, None)], method="highs")
+    return res.status == 0 and -res.fun > 1e-12
+
+
+def test_outside_states_are_outside_the_cone_and_fail_the_full_solve(oracle):
+    for u, T in OUTSIDE:
+        assert not _in_cone(oracle, u, T)
+        m = oracle.targets(np.asarray(u), T)
+        assert oracle.newton(m, oracle.gaussian_guess(np.asarray(u), T), maxit=1000)[3] == 1
+    assert _in_cone(oracle, (1.0, 0.2, 0.0), 0.5)
+
+
+def test_fallback_reproduces_the_five_invariants(oracle):
+    vel, _, _ = oracle.lattice()
+    states = list(OUTSIDE) + [(tuple(RNG.uniform(-1.2, 1.2, 3)), RNG.uniform(0.3, 1.0))
+                              for _ in range(200)]
+    for u, T in states:
+        u = np.asarray(u)
+        mu, F, n, st = oracle.newton5(u, T)
+        assert st == 0
+        want = np.r_[1.0, u, u @ u + 3 * T]
+        assert np.all(np.abs(_invariants(vel, F) - want) <= 1e-12 * np.maximum(1, np.abs(want)))
+
+
+def test_fallback_equals_full_equilibrium_at_rest(oracle):
+    """At u = 0 the isotropic exp(mu_0 + b|xi|^2) satisfies all 13 constraints (cubic symmetry
+    of the velocity set), so by uniqueness it is the 13-moment equilibrium."""
+    for T in (0.36, 0.5, 0.8, 1.1):
+        u = np.zeros(3)
+        F5 = oracle.newton5(u, T)[1]
+        lam, F13, n, st = oracle.newton(oracle.targets(u, T), oracle.gaussian_guess(u, T),
+                                        maxit=200)
+        assert st == 0
+        assert np.allclose(F5, F13, rtol=1e-12, atol=0)
+
+
+def test_collision_outside_the_cone_conserves(oracle):
+    """A failed 13-moment solve is still reported, and the collision conserves mass, momentum
+    and energy to round-off through the fallback."""
+    vel, _, _ = oracle.lattice()
+    cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
+    cv = 1.0 / (cfg.gamma - 1.0)
+    for (u, T), rho in zip(OUTSIDE, (0.954, 0.6)):
+        u = np.asarray(u)
+        F = oracle.newton5(u, T)[1]
+        f = rho * F * (1 + 1e-3 * RNG.uniform(-1, 1, 39))
+        g = (2 * cv - 3) * T * rho * F
+        lam = oracle.gaussian_guess(u, T)
+        fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f, g, lam)
+        assert st == 1
+        c2 = (vel.astype(float) ** 2).sum(1)
+        m0 = np.r_[_invariants(vel, f)[:4], f @ c2 + g.sum()]
+        m1 = np.r_[_invariants(vel, fs)[:4], fs @ c2 + gs.sum()]
+        assert np.all(np.abs(m1 - m0) <= 1e-13 * np.maximum(1, np.abs(m0))), m1 - m0
