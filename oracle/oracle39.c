@@ -269,6 +269,7 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
 #define N5 5               /* constraints of the fallback equilibrium */
 #define FALLBACK_MAXIT 50  /* Newton updates of the fallback from its Gaussian start */
 #define FALLBACK_TOL 1e-12
+#define RETRY_MAXIT 3      /* full-solve updates of a cell that holds fallback multipliers */
 
 /* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
@@ -465,14 +466,42 @@ int o39_newton5(const double *m, double *mu, double tol, int maxit, int *n_upd_o
   return status;
 }
 
-/* The fallback equilibrium F of the state (u, T) into F if its solve
- * converges (F unchanged otherwise).  Returns the fallback's status. */
-static int fallback_equilibrium(const double *u, double T, double *F) {
+/* After a fallback the cell keeps the five multipliers embedded in the 13:
+ * lam = (mu_0, mu_x, mu_y, mu_z, mu_4, mu_4, mu_4, 0, 0, -0, 0, 0, 0), for
+ * which exp(Phi lam) is the fallback equilibrium (|xi|^2 = xi_x^2 + xi_y^2 +
+ * xi_z^2).  The negative zero of lam_9 marks the embedding (it changes no
+ * exponent); a converged solve clears it (lam_9 + 0 turns -0 into +0 and
+ * leaves every other value alone), so a solved state -- even one at rest,
+ * which has the same shape -- is never taken for one.  A marked cell retries
+ * the full solve from there with RETRY_MAXIT updates, and its fallback starts
+ * from the stored mu: a cell back inside the cone converges and resumes, one
+ * still outside costs a few updates instead of a full budget. */
+static int is_fallback_embedding(const double *lam) {
+  if (!(lam[9] == 0.0 && signbit(lam[9]))) return 0;
+  for (int k = 7; k < NM; ++k)
+    if (k != 9 && (lam[k] != 0.0 || signbit(lam[k]))) return 0;
+  return memcmp(&lam[4], &lam[5], sizeof(double)) == 0 &&
+         memcmp(&lam[5], &lam[6], sizeof(double)) == 0;
+}
+
+/* The fallback for the state (u, T), from the stored mu (warm, a fallback
+ * embedding) or the Gaussian start (warm NULL).  On success lam becomes the
+ * embedding of its multipliers and F = exp(Phi lam); otherwise lam and F are
+ * left as they are.  Returns the fallback's status. */
+static int fallback_into(const double *u, double T, const double *warm, double *lam, double *F) {
   double m5[N5], mu[N5], F5[Q];
   o39_targets5(u, T, m5);
-  o39_gaussian_guess5(u, T, mu);
+  if (warm) {
+    for (int k = 0; k < N5; ++k) mu[k] = warm[k];
+  } else {
+    o39_gaussian_guess5(u, T, mu);
+  }
   if (o39_newton5(m5, mu, FALLBACK_TOL, FALLBACK_MAXIT, NULL, F5) != 0) return 1;
-  memcpy(F, F5, sizeof F5);
+  for (int k = 0; k < NM; ++k) lam[k] = 0.0;
+  for (int k = 0; k < 4; ++k) lam[k] = mu[k];
+  lam[4] = lam[5] = lam[6] = mu[4];
+  lam[9] = -0.0;
+  o39_feq_norm(lam, F);
   return 0;
 }
 
@@ -528,8 +557,13 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam,
   o39_cell_macros(p, f, g, &rho, u, &T);
   double m[NM], F[Q];
   o39_targets(u, T, m);
-  int st = o39_newton(m, lam, p->newton_tol, p->newton_maxit, p->newton_min_upd, n_upd, F);
-  if (st) fallback_equilibrium(u, T, F);
+  double lam_in[NM];
+  memcpy(lam_in, lam, sizeof lam_in);
+  const int retry = is_fallback_embedding(lam);
+  int st = o39_newton(m, lam, p->newton_tol, retry ? RETRY_MAXIT : p->newton_maxit,
+                      p->newton_min_upd, n_upd, F);
+  if (st) fallback_into(u, T, retry ? lam_in : NULL, lam, F);
+  else lam[9] += 0.0;  /* a solved state carries no embedding mark */
   double feq[Q], geq[Q];
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
@@ -560,7 +594,7 @@ int o39_equilibrium(const o39_params *p, double rho, const double *u, double T,
   o39_gaussian_guess(u, T, lam);
   int nu = 0;
   int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, &nu, F);
-  if (st) fallback_equilibrium(u, T, F);
+  if (st) fallback_into(u, T, NULL, lam, F);
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
     geq[i] = (2.0 * cv - DIM) * T * feq[i];

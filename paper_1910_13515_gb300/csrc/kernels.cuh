@@ -291,15 +291,36 @@ __device__ __forceinline__ void store_solver_state(const Desc& d, long long cell
   for (int i = 0; i < Q; ++i) st[(NM + i) * d.Np + cell] = w[WS_E + i];
 }
 
-// Where the 13-moment solve failed: the fallback equilibrium into F, or, if
-// that fails too, F back at the stored multipliers (the last accepted ones).
+// F = exp(Phi lam) at the workspace multipliers.
 template <int BLK>
-__device__ __forceinline__ void fallback_or_restore(const Desc& d, long long cell, WS<BLK> w,
-                                                    double T) {
-  if (fallback_equilibrium<BLK>(w, T)) {
-#pragma unroll 1
-    for (int i = 0; i < Q; ++i) w[WS_E + i] = d.lam[(NM + i) * d.Np + cell];
+__device__ __forceinline__ void eval_at_lam(WS<BLK> w) {
+  double G[NM];
+  eval_equilibrium<BLK>(w.at(WS_LAM), w.at(WS_DL), 0.0, w.at(WS_E), w.at(WS_M), G, false);
+}
+
+// Where the 13-moment solve failed: the fallback equilibrium, its multipliers
+// embedded in lam and F = exp(Phi lam); if that fails too, F at the last
+// accepted 13 multipliers.  retry: the cell came in with a fallback embedding,
+// whose five multipliers (still in the stored state) start the fallback.
+// state, Np: the solver-state planes (Desc::lam) and their stride.
+template <int BLK>
+__device__ __noinline__ void fallback_cell(const double* state, long long Np, long long cell,
+                                           WS<BLK> w, double T, bool retry) {
+  double warm[N5];
+  if (retry) {
+#pragma unroll
+    for (int k = 0; k < N5; ++k) warm[k] = state[k * Np + cell];
   }
+  if (fallback_equilibrium<BLK>(w, T, retry ? warm : nullptr) == 0) {
+    WS<BLK> lam = w.at(WS_LAM), mu = w.at(WS_M);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lam[k] = mu[k];
+    lam[4] = lam[5] = lam[6] = mu[4];
+#pragma unroll
+    for (int k = 7; k < NM; ++k) lam[k] = 0.0;
+    lam[9] = -0.0;  // the embedding mark
+  }
+  eval_at_lam<BLK>(w);
 }
 
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
@@ -313,9 +334,12 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   const Macro M = gather_moments<ODD, P>(d, cell, fresh_nbr<ODD>(d, c));
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
-  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, d.ph.maxit, true);
+  const bool retry = is_fallback_embedding<BLK>(lam);
+  const NewtonResult nr =
+      newton<BLK, (sizeof(P) == 4)>(w, d.ph, retry ? RETRY_MAXIT : d.ph.maxit, true);
+  if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, retry);
+  else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
-  if (nr.failed) fallback_or_restore<BLK>(d, cell, w, M.T);
   const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, c), M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
@@ -366,8 +390,8 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
       targets<BLK>(ux, uy, uz, TT, m);
       gaussian_guess<BLK>(ux, uy, uz, TT, lam);
       const NewtonResult nr = newton<BLK, false>(w, d.ph, maxit, false);
+      if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, TT, false);
       store_solver_state<BLK>(d, cell, w);
-      if (nr.failed) fallback_or_restore<BLK>(d, cell, w, TT);
       const double cgr = d.ph.cg * TT * rr;
       for (int i = 0; i < Q; ++i) {
         pop[(long long)i * d.Np + cell] = to_store<P>(d, i, rr * F[i]);

@@ -79,3 +79,43 @@ def test_collision_outside_the_cone_conserves(oracle):
         m0 = np.r_[_invariants(vel, f)[:4], f @ c2 + g.sum()]
         m1 = np.r_[_invariants(vel, fs)[:4], fs @ c2 + gs.sum()]
         assert np.all(np.abs(m1 - m0) <= 1e-13 * np.maximum(1, np.abs(m0))), m1 - m0
+
+
+def test_failed_cell_keeps_embedded_fallback_multipliers_and_retries_cheaply(oracle):
+    """After a fallback the 13 multipliers are the five embedded (lambda_4..6 equal, the rest of
+    the second and third orders zero), so exp(Phi lambda) is the fallback equilibrium; the next
+    collision of a cell still outside the cone spends at most 3 full-solve updates."""
+    vel, _, _ = oracle.lattice()
+    cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
+    cv = 1.0 / (cfg.gamma - 1.0)
+    (u, T), rho = OUTSIDE[0], 0.954
+    u = np.asarray(u)
+    F5 = oracle.newton5(u, T)[1]
+    f, g = rho * F5, (2 * cv - 3) * T * rho * F5
+    lam = oracle.gaussian_guess(u, T)
+    lam[7] = 1e-3  # not of the embedded form: a full budget
+    fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f, g, lam)
+    assert st == 1 and nu > 3
+    assert np.all(lam2[7:] == 0) and lam2[4] == lam2[5] == lam2[6]
+    assert np.signbit(lam2[9]) and not np.signbit(lam2[7])  # the embedding mark
+    F = oracle.feq_norm(lam2)
+    want = np.r_[1.0, u, u @ u + 3 * T]
+    assert np.all(np.abs(_invariants(vel, F) - want) <= 1e-12 * np.maximum(1, np.abs(want)))
+    fs2, gs2, lam3, nu2, eps2, al2, st2 = oracle.collide_cell(cfg, f, g, lam2)
+    assert st2 == 1 and nu2 <= 3
+    assert np.all(lam3[7:] == 0) and np.allclose(oracle.feq_norm(lam3), F, rtol=1e-12, atol=0)
+
+
+def test_a_solved_rest_state_is_not_taken_for_a_fallback(oracle):
+    """A cell at rest has multipliers of the embedded shape; it must keep the full Newton budget
+    when a strong change arrives (the mark, not the shape, identifies a fallback)."""
+    cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
+    cv = 1.0 / (cfg.gamma - 1.0)
+    feq, geq, lam, st = oracle.equilibrium(cfg, 1.0, np.zeros(3), 0.5)
+    assert st == 0
+    lam[7:] = 0.0           # the exact shape that symmetric arithmetic gives at rest,
+    lam[5] = lam[6] = lam[4]  # without the mark
+    # a cell at rest receives populations of a fast, hot state (a shock arriving)
+    f2, g2, _, _ = oracle.equilibrium(cfg, 2.5, np.array([0.9, 0.0, 0.0]), 0.8)
+    fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f2, g2, lam)
+    assert st == 0 and nu > 3
