@@ -270,6 +270,7 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
 #define FALLBACK_MAXIT 50  /* Newton updates of the fallback from its Gaussian start */
 #define FALLBACK_TOL 1e-12
 #define RETRY_MAXIT 3      /* full-solve updates of a cell that holds fallback multipliers */
+#define RETRY_PERIOD 8     /* such a cell retries the full solve once in this many steps */
 
 /* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
@@ -473,9 +474,11 @@ int o39_newton5(const double *m, double *mu, double tol, int maxit, int *n_upd_o
  * exponent); a converged solve clears it (lam_9 + 0 turns -0 into +0 and
  * leaves every other value alone), so a solved state -- even one at rest,
  * which has the same shape -- is never taken for one.  A marked cell retries
- * the full solve from there with RETRY_MAXIT updates, and its fallback starts
- * from the stored mu: a cell back inside the cone converges and resumes, one
- * still outside costs a few updates instead of a full budget. */
+ * the full solve from there with RETRY_MAXIT updates once every RETRY_PERIOD
+ * steps (when time + cell index / 32 is a multiple of it: groups of 32
+ * consecutive cells retry together, the groups in turn) and otherwise with
+ * none, i.e. it goes to the fallback, which starts from the stored mu.  A cell back inside the cone converges and resumes; one still
+ * outside costs a fallback solve from a close start instead of a full budget. */
 static int is_fallback_embedding(const double *lam) {
   if (!(lam[9] == 0.0 && signbit(lam[9]))) return 0;
   for (int k = 7; k < NM; ++k)
@@ -547,9 +550,10 @@ void o39_cell_macros(const o39_params *p, const double *f, const double *g,
 /* One BGK collision of one fluid cell (Sec. 3 and Eq. DeltaAvg / alpha):
  * macros -> MB targets -> Newton (warm start lam) -> f^eq, g^eq = (2C_v-D) T f^eq
  * -> eps, alpha -> h* = h - (h - h^eq)/(tau alpha) for h = f and h = g.
+ * phase: time step + cell index / 32 (it schedules the retries of fallback cells).
  * reading: eps uses f only and the same alpha relaxes f and g (Pr = 1).
  * In place on f, g, lam.  Returns the Newton status. */
-int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam,
+int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, int64_t phase,
                      int *n_upd, double *eps_out, double *alpha_out) {
   build_lattice();
   double cv = 1.0 / (p->gamma - 1.0);
@@ -559,11 +563,16 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam,
   o39_targets(u, T, m);
   double lam_in[NM];
   memcpy(lam_in, lam, sizeof lam_in);
-  const int retry = is_fallback_embedding(lam);
-  int st = o39_newton(m, lam, p->newton_tol, retry ? RETRY_MAXIT : p->newton_maxit,
-                      p->newton_min_upd, n_upd, F);
-  if (st) fallback_into(u, T, retry ? lam_in : NULL, lam, F);
-  else lam[9] += 0.0;  /* a solved state carries no embedding mark */
+  const int marked = is_fallback_embedding(lam);
+  /* a marked cell off its retry step gets no update: it stays on the fallback
+   * unless its embedding already meets the 13 constraints */
+  const int maxit = !marked ? p->newton_maxit : (phase % RETRY_PERIOD == 0 ? RETRY_MAXIT : 0);
+  int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
+  if (st) {  /* counted as a failure: the cell is on the fallback this step */
+    if (fallback_into(u, T, marked ? lam_in : NULL, lam, F)) o39_feq_norm(lam, F);
+  } else {
+    lam[9] += 0.0;  /* a solved state carries no embedding mark */
+  }
   double feq[Q], geq[Q];
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
@@ -691,7 +700,7 @@ void o39_stream(const o39_params *p, const uint8_t *mask, const double *fpost,
 /* nsteps full time steps: collide every fluid cell, then stream (pull) from
  * the post-collision array back into f, g.  Returns failed Newton solves. */
 int64_t o39_step(const o39_params *p, const uint8_t *mask, double *f, double *g,
-                 double *lam, int nsteps, o39_stats *st) {
+                 double *lam, int64_t t0, int nsteps, o39_stats *st) {
   build_lattice();
   int64_t N = (int64_t)p->nx * p->ny * p->nz;
   double *fp = (double *)malloc(sizeof(double) * N * Q);
@@ -708,7 +717,8 @@ int64_t o39_step(const o39_params *p, const uint8_t *mask, double *f, double *g,
       if (mask[c] != M_FLUID) continue;
       int nu = 0;
       double eps, alpha;
-      failed += o39_collide_cell(p, fp + c * Q, gp + c * Q, lam + c * NM, &nu, &eps, &alpha);
+      failed += o39_collide_cell(p, fp + c * Q, gp + c * Q, lam + c * NM, t0 + t + (c >> 5), &nu,
+                                 &eps, &alpha);
       upd += nu;
       fluid += 1;
       int b = nu < 31 ? nu : 31;

@@ -95,14 +95,14 @@ def lib():
         _lib.o39_targets5.restype = None
         _lib.o39_gaussian_guess5.argtypes = [vp, d, vp]
         _lib.o39_gaussian_guess5.restype = None
-        _lib.o39_collide_cell.argtypes = [P, vp, vp, vp, vp, vp, vp]
+        _lib.o39_collide_cell.argtypes = [P, vp, vp, vp, i64, vp, vp, vp]
         _lib.o39_collide_cell.restype = ctypes.c_int
         _lib.o39_equilibrium.argtypes = [P, d, vp, d, vp, vp, vp, ctypes.c_int]
         _lib.o39_equilibrium.restype = ctypes.c_int
         _lib.o39_init.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         _lib.o39_init.restype = i64
         _lib.o39_stream.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
-        _lib.o39_step.argtypes = [P, vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(Stats)]
+        _lib.o39_step.argtypes = [P, vp, vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
         _lib.o39_step.restype = i64
         _lib.o39_macros.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
         _lib.o39_conserved.argtypes = [P, vp, vp, vp, vp]
@@ -258,8 +258,9 @@ def cell_macros(cfg: Config, f, g):
     return rho.value, u, T.value
 
 
-def collide_cell(cfg: Config, f, g, lam):
-    """One collision in place on copies; returns (f*, g*, lam, n_upd, eps, alpha, status)."""
+def collide_cell(cfg: Config, f, g, lam, phase: int = 0):
+    """One collision in place on copies; returns (f*, g*, lam, n_upd, eps, alpha, status).
+    phase (time step + cell index / 32) schedules the retries of a cell on the fallback."""
     f = _f64(f).copy()
     g = _f64(g).copy()
     lam = _f64(lam).copy()
@@ -267,7 +268,8 @@ def collide_cell(cfg: Config, f, g, lam):
     eps = ctypes.c_double()
     al = ctypes.c_double()
     p = cfg.params()
-    st = lib().o39_collide_cell(ctypes.byref(p), _p(f), _p(g), _p(lam), ctypes.byref(nu),
+    st = lib().o39_collide_cell(ctypes.byref(p), _p(f), _p(g), _p(lam), int(phase),
+                                ctypes.byref(nu),
                                 ctypes.byref(eps), ctypes.byref(al))
     return f, g, lam, nu.value, eps.value, al.value, st
 
@@ -322,7 +324,7 @@ def init(cfg: Config, mask, rho, u, T, allow_failed: bool = False) -> State:
 def step(st: State, nsteps: int) -> int:
     p = st.cfg.params()
     failed = lib().o39_step(ctypes.byref(p), _p(st.mask), _p(st.f), _p(st.g), _p(st.lam),
-                            int(nsteps), ctypes.byref(st.stats))
+                            int(st.t), int(nsteps), ctypes.byref(st.stats))
     st.t += nsteps
     return int(failed)
 

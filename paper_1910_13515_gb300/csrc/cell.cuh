@@ -357,9 +357,12 @@ constexpr double FALLBACK_TOL = 1e-12;
 // the embedding (it changes no exponent); a converged solve clears it (lam_9 + 0
 // turns -0 into +0 and leaves any other value alone), so a solved state, even
 // one at rest with the same shape, is never taken for one.  A marked cell
-// retries the full solve from there with RETRY_MAXIT updates, and its fallback
-// starts from the stored mu.
+// retries the full solve from there with RETRY_MAXIT updates once every
+// RETRY_PERIOD steps (when time + cell index / 32 is a multiple of it: the 32
+// cells of a warp retry together, the warps in turn) and otherwise goes
+// straight to the fallback, which starts from the stored mu.
 constexpr int RETRY_MAXIT = 3;
+constexpr int RETRY_PERIOD = 8;  // a power of two
 
 // F = exp(phi5 . (mu - t dl)) (t = 0: mu itself) and G = sum_i F_i phi5(xi_i) - m5.
 template <int BLK>

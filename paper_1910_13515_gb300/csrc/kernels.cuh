@@ -38,6 +38,7 @@ struct Desc {
   const double* href;                 // 78 reference populations (precision form)
   double mref[5];                     // sum of href: rho, j, sum f|xi|^2 + sum g
   long long N, Np;                    // cells, plane stride in elements
+  long long t;                        // time step being taken (schedules fallback retries)
   int nx, ny, nz;
   int per[3];                         // periodic axes
   Phys ph;
@@ -298,10 +299,12 @@ __device__ __forceinline__ void eval_at_lam(WS<BLK> w) {
   eval_equilibrium<BLK>(w.at(WS_LAM), w.at(WS_DL), 0.0, w.at(WS_E), w.at(WS_M), G, false);
 }
 
-// Where the 13-moment solve failed: the fallback equilibrium, its multipliers
-// embedded in lam and F = exp(Phi lam); if that fails too, F at the last
-// accepted 13 multipliers.  retry: the cell came in with a fallback embedding,
-// whose five multipliers (still in the stored state) start the fallback.
+// Where the 13-moment solve failed or took no update: the fallback's
+// multipliers embedded in lam (lam unchanged if that fails too), and F =
+// exp(Phi lam) evaluated as the full solve does, so the cached F stays exact
+// (for an embedding it is the fallback equilibrium up to rounding).  retry:
+// the cell came in with a fallback embedding, whose five multipliers (still in
+// the stored state) start the fallback.
 // state, Np: the solver-state planes (Desc::lam) and their stride.
 template <int BLK>
 __device__ __noinline__ void fallback_cell(const double* state, long long Np, long long cell,
@@ -320,7 +323,7 @@ __device__ __noinline__ void fallback_cell(const double* state, long long Np, lo
     for (int k = 7; k < NM; ++k) lam[k] = 0.0;
     lam[9] = -0.0;  // the embedding mark
   }
-  eval_at_lam<BLK>(w);
+  eval_at_lam<BLK>(w);  // F = exp(Phi lam), the cached value the next solve starts from
 }
 
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
@@ -334,10 +337,13 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   const Macro M = gather_moments<ODD, P>(d, cell, fresh_nbr<ODD>(d, c));
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
-  const bool retry = is_fallback_embedding<BLK>(lam);
-  const NewtonResult nr =
-      newton<BLK, (sizeof(P) == 4)>(w, d.ph, retry ? RETRY_MAXIT : d.ph.maxit, true);
-  if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, retry);
+  const bool marked = is_fallback_embedding<BLK>(lam);
+  // a marked cell off its retry step gets no update (it stays on the fallback
+  // unless its embedding already meets the 13 constraints)
+  const int maxit =
+      !marked ? d.ph.maxit : (((d.t + (cell >> 5)) & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0);
+  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, maxit, true);
+  if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
   const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, c), M, F);
@@ -636,6 +642,7 @@ __global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict
   if (threadIdx.x == 0) {
     sd = E[tl.lat].d;
     st = E[tl.lat].t0 + s < E[tl.lat].t_end ? E[tl.lat].t0 + s : -1;
+    sd.t = st;
   }
   for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
   load_exp_table();  // also publishes sd and st

@@ -104,6 +104,7 @@ static int last_launch() { return cudaGetLastError() == cudaSuccess ? LBM39_OK :
 template <class P>
 struct Launch {
   static void step(lbm39_lattice* L, bool odd) {
+    L->desc.t = L->t;
     const unsigned grid = (unsigned)((L->N + BLK - 1) / BLK);
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
     if (!odd) {

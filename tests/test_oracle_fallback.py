@@ -119,3 +119,22 @@ def test_a_solved_rest_state_is_not_taken_for_a_fallback(oracle):
     f2, g2, _, _ = oracle.equilibrium(cfg, 2.5, np.array([0.9, 0.0, 0.0]), 0.8)
     fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f2, g2, lam)
     assert st == 0 and nu > 3
+
+
+def test_marked_cell_retries_only_on_its_phase(oracle):
+    """A cell on the fallback tries the full solve (3 updates) only when time + cell index / 32
+    is a multiple of 8; on other steps it takes the fallback directly (no update, still
+    counted)."""
+    cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
+    cv = 1.0 / (cfg.gamma - 1.0)
+    (u, T), rho = OUTSIDE[0], 0.954
+    u = np.asarray(u)
+    F5 = oracle.newton5(u, T)[1]
+    f, g = rho * F5, (2 * cv - 3) * T * rho * F5
+    lam = oracle.gaussian_guess(u, T)
+    lam[7] = 1e-3
+    lam2 = oracle.collide_cell(cfg, f, g, lam)[2]
+    assert np.signbit(lam2[9])
+    for phase, most in ((1, 0), (7, 0), (8, 3), (16, 3)):
+        _, _, lam3, nu, _, _, st = oracle.collide_cell(cfg, f, g, lam2, phase=phase)
+        assert st == 1 and nu <= most and np.signbit(lam3[9])
