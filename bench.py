@@ -46,10 +46,10 @@ FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0)}
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the kernel sources they were
 # captured with; reported as null once the sources differ (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": "13745a14ea1ab14e",
-               "gb_per_launch": {"naca/fp64": 4.459, "naca/mixed": 3.174,
-                                 "box128/fp64": 5.649, "box128/mixed": 3.208,
-                                 "box256/fp64": 45.19, "box256/mixed": 25.66,
+NCU_TRAFFIC = {"kernel_hash": "59df799a90bc3db9",
+               "gb_per_launch": {"naca/fp64": 4.461, "naca/mixed": 3.176,
+                                 "box128/fp64": 5.687, "box128/mixed": 3.208,
+                                 "box256/fp64": 45.50, "box256/mixed": 25.66,
                                  "box384/mixed": 86.62}}
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                   "lbm39.cu")
