@@ -145,12 +145,18 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
  * moments -> Maxwell-Boltzmann targets -> Newton from the previous step's
  * multipliers -> f^eq, g^eq -> eps, alpha -> BGK on f and g -> streaming by
  * shifts of up to 3 cells with the mask rules).  In-place (AA pattern):
- * even and odd steps use two kernels over one population buffer. */
+ * even and odd steps use two kernels over one population buffer.
+ * A cell whose 13 targets lie outside the moment cone of the 39 velocities
+ * has no 13-moment equilibrium; its solve fails, and the cell relaxes to the
+ * maximum-entropy equilibrium of the five collision invariants instead
+ * (conserving mass, momentum and energy), retrying the full solve once every
+ * 8 steps.  Each such cell-step counts as a failure (lbm39_sync). */
 int lbm39_step(lbm39_lattice* L, int64_t nsteps);
 
 /* Waits for the lattice's stream for at most timeout_us microseconds (< 0:
  * no limit).  *failed_cells (may be NULL) receives the Newton failures
- * since lbm39_init.  Returns LBM39_ERR_TIMEOUT if the work is still running,
+ * since lbm39_init, summed over cells and steps (cell-steps that took the
+ * five-invariant fallback equilibrium, see lbm39_step).  Returns LBM39_ERR_TIMEOUT if the work is still running,
  * LBM39_ERR_NEWTON if failed_cells > 0, else LBM39_OK. */
 int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells);
 
