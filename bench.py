@@ -366,6 +366,12 @@ def main():
     st1 = L.stats()
     cell_steps = fluid * args.steps
     k_upd = (st1.newton_updates - st0.newton_updates) / cell_steps
+    # share of cell updates by Newton update count (0, 1, 2, 3, >= 4) and by branch of
+    # alpha(eps) (eps < 1e-2, < 1e-1, < 1, >= 1), over the timed steps
+    hist = [st1.newton_hist[k] - st0.newton_hist[k] for k in range(32)]
+    upd_share = [round(h / cell_steps, 4) for h in hist[:4]] + [round(sum(hist[4:]) / cell_steps, 4)]
+    eps_share = [round((st1.eps_hist[k] - st0.eps_hist[k]) / cell_steps, 4) for k in range(4)]
+    failed_share = round((st1.failed_cells - st0.failed_cells) / cell_steps, 6)
     value = units / elapsed_s / 1e6
 
     # dominant kernel (the fused step): per-launch duration on its own stream
@@ -469,6 +475,9 @@ def main():
                        "cells": N, "fluid_cells": int(fluid),
                        "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
                        "newton_updates_per_cell": round(k_upd, 4),
+                       "newton_updates_share_0_1_2_3_4plus": upd_share,
+                       "alpha_branch_share": eps_share,
+                       "fallback_share": failed_share,
                        "l2": "inputs larger than L2 (%.2f GB of populations)" % (
                            BYTES_PER_UPDATE[args.precision] / 2 * N / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
