@@ -34,6 +34,9 @@ WORKLOADS = {
               "seed 0, tau=0.55, alpha(eps) on",
     "box128": "3-D periodic box 128^3 (profiling size), solenoidal velocity rms Ma=0.8, "
               "+-5% rho/T noise, seed 0, tau=0.55, alpha(eps) on",
+    "box2d": "quasi-2-D periodic box 2048x1024x1, solenoidal velocity scaled to rms Ma=0.8 with "
+             "u_z then set to 0 (z-mirror symmetric), +-5% rho/T noise, seed 0, tau=0.55, "
+             "alpha(eps) on",
     "sod": "Sod tube 400x1x1, outflow ends, tau=0.5 with alpha(eps)",
     "serve": "serving form: Poisson stream of 64 seeded requests (Riemann tubes 200-4000 cells, "
              "2-D shear layers 128^2-1024^2, 200-2000 steps), admitted into a 4 GiB budget",
@@ -42,15 +45,18 @@ WORKLOADS = {
 # FP64 arithmetic of one fluid-cell update as executed by the step kernel, from ncu
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL) on two workloads with different
 # Newton work: A + B * (Newton updates per cell).  See profiles/.
-FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0)}
+FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0),
+                    # the nine-constraint (z-mirror) solve of lattices one cell thick in z
+                    "fp64_2d": (650.0, 1470.0)}
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the kernel sources they were
 # captured with; reported as null once the sources differ (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": "59df799a90bc3db9",
-               "gb_per_launch": {"naca/fp64": 4.461, "naca/mixed": 3.176,
-                                 "box128/fp64": 5.687, "box128/mixed": 3.208,
-                                 "box256/fp64": 45.50, "box256/mixed": 25.66,
-                                 "box384/mixed": 86.62}}
+NCU_TRAFFIC = {"kernel_hash": "cc58b67388908212",
+               "gb_per_launch": {"naca/fp64": 4.309, "naca/mixed": 3.177,
+                                 "box128/fp64": 5.670, "box128/mixed": 3.207,
+                                 "box2d/fp64": 4.583,
+                                 "box256/fp64": 45.36, "box256/mixed": 25.66,
+                                 "box384/mixed": 86.59}}
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                   "lbm39.cu")
 
@@ -87,6 +93,10 @@ def make_setup(name: str, mach: float = 0.8):
         return inputs.box(n=384, seed=0, mach_rms=mach)
     if name == "box128":
         return inputs.box(n=128, seed=0, mach_rms=mach)
+    if name == "box2d":
+        s = inputs.box(seed=0, mach_rms=mach, shape=(1, 1024, 2048))
+        s.u[2] = 0.0  # in-plane flow: z-mirror symmetric
+        return s
     if name == "sod":
         return inputs.sod(400)
     raise ValueError(name)
@@ -380,7 +390,10 @@ def main():
     rc, peak_tf = C.lbm39_selftest_dfma(scratch.data_ptr(), scratch.numel() * 8,
                                         stream.cuda_stream)
     C.check(rc, "lbm39_selftest_dfma")
-    model = FP64_FLOPS_MODEL[args.precision]
+    # lattices one cell thick in z with u_z = 0 take the nine-constraint (z-mirror) solve
+    reduced = (args.precision == "fp64" and s.nz == 1 and not np.any(s.u[2])
+               and s.u_inf[2] == 0.0)
+    model = FP64_FLOPS_MODEL["fp64_2d" if reduced else args.precision]
     achieved_tf = None
     if model is not None:
         achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12

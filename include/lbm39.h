@@ -34,9 +34,10 @@
  * - Errors: every int-returning call returns LBM39_OK (0) or a negative
  *   lbm39_status; nothing is thrown across the ABI.  lbm39_strerror names
  *   the code.  Calls on one lattice are not thread-safe.
- * - Asynchrony: lbm39_init, lbm39_step and lbm39_read enqueue work on the
- *   lattice's stream and return; lbm39_sync, lbm39_stats and the *_host
- *   calls wait for it.
+ * - Asynchrony: lbm39_step and lbm39_read enqueue work on the lattice's
+ *   stream and return; lbm39_init, lbm39_sync, lbm39_stats and the *_host
+ *   calls wait for it (lbm39_init reads back whether the initial state allows
+ *   the z-mirror reduction of lbm39_params.reduce_2d).
  */
 #ifndef LBM39_H
 #define LBM39_H
@@ -83,6 +84,12 @@ typedef struct {
   int32_t precision;        /* lbm39_precision */
   double ref_rho, ref_T;    /* LBM39_MIXED reference state (rho_bar, T_bar) */
   double rho_inf, u_inf[3], T_inf; /* far-field state held by freestream cells */
+  int32_t reduce_2d;        /* 1 (default): on a lattice one cell thick in z whose initial
+                               u_z and u_inf[2] are all 0, the populations stay mirror
+                               symmetric in z, and the FP64 Newton solve uses the nine
+                               z-even constraints (the others are exactly zero there):
+                               the same values, less work.  0: always all 13.  The
+                               precision form always solves all 13. */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;

@@ -133,26 +133,31 @@ __device__ __noinline__ void exp_all_slow(double* Fp) {
 
 // F_i = exp(sum_k lam_k phi_k(xi_i)) (Eq. discrete-equilibrium / rho) into F,
 // and the constraint residual G_k = sum_i F_i phi_k(xi_i) - m_k (Eq. constraints).
-// The evaluation point is lam - t dl (t = 0: lam itself, dl not read).
+// The evaluation point is lam - t dl (t = 0: lam itself, dl not read); dl holds
+// the direction of the system's multipliers (Sys<D2>: all 13, or the nine
+// z-even ones, whose G this returns).
 // from_F: F already holds exp(Phi lam) (kept from the previous step), so only
 // the moments are formed -- the same numbers, bit for bit, as evaluating again.
-template <int BLK>
+// D2: z-mirrored velocities share their exponential.
+template <int BLK, bool D2 = false>
 __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double t, WS<BLK> F,
-                                                 WS<BLK> m, double (&G)[NM], bool from_F) {
+                                                 WS<BLK> m, double (&G)[Sys<D2>::N],
+                                                 bool from_F) {
+  using S = Sys<D2>;
   double x[Q];
   if (from_F) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) x[i] = F[i];
   } else {
     double l[NM];
-    if (t == 0.0) {
 #pragma unroll
-      for (int k = 0; k < NM; ++k) l[k] = lam[k];
-    } else {
+    for (int k = 0; k < NM; ++k) l[k] = lam[k];
+    if (t != 0.0) {
 #pragma unroll
-      for (int k = 0; k < NM; ++k) l[k] = fma(-t, dl[k], lam[k]);
+      for (int k = 0; k < S::N; ++k) l[S::idx(k)] = fma(-t, dl[k], lam[S::idx(k)]);
     }
-    gen::exponents(l, x);
+    if constexpr (D2) gen::exponents2d(l, x);
+    else gen::exponents(l, x);
     int wide = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
@@ -163,46 +168,50 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
 #pragma unroll
       for (int i = 0; i < Q; ++i) x[i] = F[i];
     } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        x[i] = exp_tang_core(x[i]);
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (D2 && zmirror(i) < i) x[i] = x[zmirror(i)];
+        else x[i] = exp_tang_core(x[i]);
         F[i] = x[i];
-      }
+      });
     }
   }
-  double s[NM];
-  gen::moments_s<double>(x, s);
+  double s[S::N];
+  if constexpr (D2) gen::moments_s2d<double>(x, s);
+  else gen::moments_s<double>(x, s);
 #pragma unroll
-  for (int k = 0; k < NM; ++k) G[k] = s[k] - m[k];
+  for (int k = 0; k < S::N; ++k) G[k] = s[k] - m[S::idx(k)];
 }
 
-__device__ __forceinline__ double max_abs(const double (&v)[NM]) {
+template <int N>
+__device__ __forceinline__ double max_abs(const double (&v)[N]) {
   double r = 0.0;
 #pragma unroll
-  for (int k = 0; k < NM; ++k) {
+  for (int k = 0; k < N; ++k) {
     const double a = fabs(v[k]);
     r = (a <= r) ? r : a;  // NaN propagates
   }
   return r;
 }
 
-__device__ __forceinline__ double sum_sq(const double (&v)[NM]) {
+template <int N>
+__device__ __forceinline__ double sum_sq(const double (&v)[N]) {
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < NM; ++k) s = fma(v[k], v[k], s);
+  for (int k = 0; k < N; ++k) s = fma(v[k], v[k], s);
   return s;
 }
 
 // In-place LDL^T of a packed symmetric 13x13 J (unit-lower L below a diagonal
 // D) and the solve J x = b (b overwritten by x).  False if a pivot is not
 // positive (J not numerically SPD).
-template <class T>
-__device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
+template <class T, int N = NM>
+__device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
   bool ok = true;
-  T rd[NM];
-  static_for<0, NM>([&](auto JJ) {
+  T rd[N];
+  static_for<0, N>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
-    T v[NM];
+    T v[N];
     static_for<0, j>([&](auto K) {
       constexpr int k = decltype(K)::value;
       v[k] = J[tri(j, k)] * J[tri(k, k)];
@@ -215,7 +224,7 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
     ok = ok && (dj > T(0));
     J[tri(j, j)] = dj;
     rd[j] = recip(dj);
-    static_for<j + 1, NM>([&](auto II) {
+    static_for<j + 1, N>([&](auto II) {
       constexpr int i = decltype(II)::value;
       T a = J[tri(i, j)];
       static_for<0, j>([&](auto K) {
@@ -225,7 +234,7 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
       J[tri(i, j)] = a * rd[j];
     });
   });
-  static_for<1, NM>([&](auto II) {  // L y = b
+  static_for<1, N>([&](auto II) {  // L y = b
     constexpr int i = decltype(II)::value;
     T a = b[i];
     static_for<0, i>([&](auto K) {
@@ -235,11 +244,11 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
     b[i] = a;
   });
 #pragma unroll
-  for (int i = 0; i < NM; ++i) b[i] *= rd[i];  // D z = y
-  static_for<0, NM - 1>([&](auto II) {  // L^T x = z
-    constexpr int i = NM - 2 - decltype(II)::value;
+  for (int i = 0; i < N; ++i) b[i] *= rd[i];  // D z = y
+  static_for<0, N - 1>([&](auto II) {  // L^T x = z
+    constexpr int i = N - 2 - decltype(II)::value;
     T a = b[i];
-    static_for<i + 1, NM>([&](auto K) {
+    static_for<i + 1, N>([&](auto K) {
       constexpr int k = decltype(K)::value;
       a = fma(-J[tri(k, i)], b[k], a);
     });
@@ -252,27 +261,30 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[NTRI], T (&b)[NM]) {
 // b and delta in dl.  FP64 path: J and LDL^T in FP64.  Precision form: in
 // FP32 (the residual and the update stay FP64, so the iteration still
 // converges to the FP64 root).
-template <int BLK, bool MIXED>
+template <int BLK, bool MIXED, bool D2 = false>
 __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
+  constexpr int N = Sys<D2>::N;
   if constexpr (!MIXED) {
-    double J[NTRI], s[NM], b[NM];
-    gen::moments<double>(F, s, J);
+    double J[N * (N + 1) / 2], s[N], b[N];
+    if constexpr (D2) gen::moments2d<double>(F, s, J);
+    else gen::moments<double>(F, s, J);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) b[k] = dl[k];
-    const bool ok = ldlt_solve<double>(J, b);
+    for (int k = 0; k < N; ++k) b[k] = dl[k];
+    const bool ok = ldlt_solve<double, N>(J, b);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) dl[k] = b[k];
+    for (int k = 0; k < N; ++k) dl[k] = b[k];
     return ok;
   } else {
-    float Ff[Q], J[NTRI], s[NM], bf[NM];
+    float Ff[Q], J[N * (N + 1) / 2], s[N], bf[N];
 #pragma unroll
     for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
-    gen::moments<float>(Ff, s, J);
+    if constexpr (D2) gen::moments2d<float>(Ff, s, J);
+    else gen::moments<float>(Ff, s, J);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) bf[k] = trunc_float(dl[k]);
-    const bool ok = ldlt_solve<float>(J, bf);
+    for (int k = 0; k < N; ++k) bf[k] = trunc_float(dl[k]);
+    const bool ok = ldlt_solve<float, N>(J, bf);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) dl[k] = exact_double(bf[k]);
+    for (int k = 0; k < N; ++k) dl[k] = exact_double(bf[k]);
     return ok;
   }
 }
@@ -295,15 +307,16 @@ struct NewtonResult {
 // cached: F already holds exp(Phi lam) for the starting lam (the previous
 // step's last evaluation, kept per cell), so the first evaluation skips the
 // exponentials.
-template <int BLK, bool MIXED>
+template <int BLK, bool MIXED, bool D2 = false>
 __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached) {
+  using S = Sys<D2>;
   WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), dl = w.at(WS_DL);
   int n = 0, failed = 0, ls = 0;
   bool first = true, polished = false, restore = false;
   double t = 0.0, s0 = 0.0;  // trial point lam - t dl
   for (;;) {
-    double G[NM];
-    eval_equilibrium<BLK>(lam, dl, t, F, m, G, first && cached);
+    double G[S::N];
+    eval_equilibrium<BLK, D2>(lam, dl, t, F, m, G, first && cached);
     if (restore) break;  // F is back at the last accepted lam after a failed line search
     if (!first && !polished && !(sum_sq(G) < s0)) {  // reject: halve the step
       if (++ls > LS_MAX) {
@@ -318,7 +331,7 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
     // accept the trial point
     if (t != 0.0) {
 #pragma unroll
-      for (int k = 0; k < NM; ++k) lam[k] = fma(-t, dl[k], lam[k]);
+      for (int k = 0; k < S::N; ++k) lam[S::idx(k)] = fma(-t, dl[k], lam[S::idx(k)]);
     }
     if (!first) ++n;
     first = false;
@@ -327,8 +340,8 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
     if (n >= maxit) { failed = 1; break; }
     s0 = sum_sq(G);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) dl[k] = G[k];
-    if (!newton_direction<BLK, MIXED>(F, dl)) { failed = 1; break; }
+    for (int k = 0; k < S::N; ++k) dl[k] = G[k];
+    if (!newton_direction<BLK, MIXED, D2>(F, dl)) { failed = 1; break; }
     polished = r < ph.tol;
     t = 1.0;
     ls = 0;

@@ -55,6 +55,29 @@ constexpr int phi(int k, int i) {
 constexpr int tri(int k, int l) { return k * (k + 1) / 2 + l; }
 constexpr int NTRI = NM * (NM + 1) / 2;
 
+// Velocity with the z component reversed.
+constexpr int zmirror(int i) {
+  for (int j = 0; j < Q; ++j)
+    if (CX[j] == CX[i] && CY[j] == CY[i] && CZ[j] == -CZ[i]) return j;
+  return i;
+}
+
+// The constraint system solved per cell: all 13 multipliers, or (D2) the nine
+// basis functions even in xi_z.  On a lattice one cell thick in z whose
+// populations are z-mirror symmetric (u_z = 0 everywhere), the z-odd residuals
+// and the couplings of the z-odd multipliers are exact zeros, so those
+// multipliers stay exactly zero and leaving them out changes no value.
+// (z-even indices 0, 1, 2, 4, 5, 6, 7, 10, 11 by arithmetic: the map is also
+// evaluated at run time in device code, where a host array does not exist)
+template <bool D2>
+struct Sys {
+  static constexpr int N = D2 ? 9 : NM;
+  static constexpr int idx(int k) { return !D2 ? k : k < 3 ? k : k < 7 ? k + 1 : k + 3; }
+};
+static_assert(Sys<true>::idx(0) == 0 && Sys<true>::idx(3) == 4 && Sys<true>::idx(6) == 7 &&
+                  Sys<true>::idx(7) == 10 && Sys<true>::idx(8) == 11,
+              "z-even basis indices");
+
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
 template <int B, int E, class Fn>
 __device__ __forceinline__ void static_for(Fn&& f) {

@@ -4,6 +4,10 @@
 namespace lbm39 {
 namespace gen {
 
+// Rounded products that are never contracted into a fused multiply-add.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 // e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium).
 __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]) {
   const double c0_0 = l[0];
@@ -15,13 +19,13 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[5] = t1_0_0;
   e[6] = t1_0_1;
   const double c2_0 = fma(double(4), l[6], l[0]);
-  const double c2_z = fma(double(8), l[12], double(2) * l[3]);
+  const double c2_z = fma(double(8), l[12], mul_rn(double(2), l[3]));
   const double t2_0_0 = c2_0 + c2_z;
   const double t2_0_1 = c2_0 - c2_z;
   e[19] = t2_0_0;
   e[20] = t2_0_1;
   const double c3_0 = fma(double(9), l[6], l[0]);
-  const double c3_z = fma(double(27), l[12], double(3) * l[3]);
+  const double c3_z = fma(double(27), l[12], mul_rn(double(3), l[3]));
   const double t3_0_0 = c3_0 + c3_z;
   const double t3_0_1 = c3_0 - c3_z;
   e[37] = t3_0_0;
@@ -33,15 +37,15 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[3] = t4_0_0;
   e[4] = t4_0_1;
   const double c5_0 = fma(double(4), l[5], l[0]);
-  const double c5_y = fma(double(8), l[11], double(2) * l[2]);
+  const double c5_y = fma(double(8), l[11], mul_rn(double(2), l[2]));
   const double t5_0_0 = c5_0 + c5_y;
   const double t5_0_1 = c5_0 - c5_y;
   e[17] = t5_0_0;
   e[18] = t5_0_1;
   const double c6_0 = fma(double(4), l[6], fma(double(4), l[5], l[0]));
-  const double c6_y = fma(double(16), l[11], double(2) * l[2]);
-  const double c6_z = fma(double(16), l[12], double(2) * l[3]);
-  const double c6_yz = double(4) * l[9];
+  const double c6_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
+  const double c6_z = fma(double(16), l[12], mul_rn(double(2), l[3]));
+  const double c6_yz = mul_rn(double(4), l[9]);
   const double t6_0_0 = c6_0 + c6_y;
   const double t6_0_1 = c6_0 - c6_y;
   const double t6_0_2 = c6_z + c6_yz;
@@ -55,7 +59,7 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[32] = t6_1_2;
   e[30] = t6_1_3;
   const double c7_0 = fma(double(9), l[5], l[0]);
-  const double c7_y = fma(double(27), l[11], double(3) * l[2]);
+  const double c7_y = fma(double(27), l[11], mul_rn(double(3), l[2]));
   const double t7_0_0 = c7_0 + c7_y;
   const double t7_0_1 = c7_0 - c7_y;
   e[35] = t7_0_0;
@@ -104,15 +108,15 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[10] = t9_2_6;
   e[8] = t9_2_7;
   const double c10_0 = fma(double(4), l[4], l[0]);
-  const double c10_x = fma(double(8), l[10], double(2) * l[1]);
+  const double c10_x = fma(double(8), l[10], mul_rn(double(2), l[1]));
   const double t10_0_0 = c10_0 + c10_x;
   const double t10_0_1 = c10_0 - c10_x;
   e[15] = t10_0_0;
   e[16] = t10_0_1;
   const double c11_0 = fma(double(4), l[6], fma(double(4), l[4], l[0]));
-  const double c11_x = fma(double(16), l[10], double(2) * l[1]);
-  const double c11_z = fma(double(16), l[12], double(2) * l[3]);
-  const double c11_xz = double(4) * l[8];
+  const double c11_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
+  const double c11_z = fma(double(16), l[12], mul_rn(double(2), l[3]));
+  const double c11_xz = mul_rn(double(4), l[8]);
   const double t11_0_0 = c11_0 + c11_x;
   const double t11_0_1 = c11_0 - c11_x;
   const double t11_0_2 = c11_z + c11_xz;
@@ -126,9 +130,9 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[28] = t11_1_2;
   e[26] = t11_1_3;
   const double c12_0 = fma(double(4), l[5], fma(double(4), l[4], l[0]));
-  const double c12_x = fma(double(16), l[10], double(2) * l[1]);
-  const double c12_y = fma(double(16), l[11], double(2) * l[2]);
-  const double c12_xy = double(4) * l[7];
+  const double c12_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
+  const double c12_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
+  const double c12_xy = mul_rn(double(4), l[7]);
   const double t12_0_0 = c12_0 + c12_x;
   const double t12_0_1 = c12_0 - c12_x;
   const double t12_0_2 = c12_y + c12_xy;
@@ -142,7 +146,110 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[24] = t12_1_2;
   e[22] = t12_1_3;
   const double c13_0 = fma(double(9), l[4], l[0]);
-  const double c13_x = fma(double(27), l[10], double(3) * l[1]);
+  const double c13_x = fma(double(27), l[10], mul_rn(double(3), l[1]));
+  const double t13_0_0 = c13_0 + c13_x;
+  const double t13_0_1 = c13_0 - c13_x;
+  e[33] = t13_0_0;
+  e[34] = t13_0_1;
+}
+
+// The same with the z-odd multipliers zero (lattice one cell thick in z, u_z = 0).
+__device__ __forceinline__ void exponents2d(const double (&l)[13], double (&e)[39]) {
+  const double c0_0 = l[0];
+  e[0] = c0_0;
+  const double c1_0 = l[0] + l[6];
+  e[5] = c1_0;
+  e[6] = c1_0;
+  const double c2_0 = fma(double(4), l[6], l[0]);
+  e[19] = c2_0;
+  e[20] = c2_0;
+  const double c3_0 = fma(double(9), l[6], l[0]);
+  e[37] = c3_0;
+  e[38] = c3_0;
+  const double c4_0 = l[0] + l[5];
+  const double c4_y = l[2] + l[11];
+  const double t4_0_0 = c4_0 + c4_y;
+  const double t4_0_1 = c4_0 - c4_y;
+  e[3] = t4_0_0;
+  e[4] = t4_0_1;
+  const double c5_0 = fma(double(4), l[5], l[0]);
+  const double c5_y = fma(double(8), l[11], mul_rn(double(2), l[2]));
+  const double t5_0_0 = c5_0 + c5_y;
+  const double t5_0_1 = c5_0 - c5_y;
+  e[17] = t5_0_0;
+  e[18] = t5_0_1;
+  const double c6_0 = fma(double(4), l[6], fma(double(4), l[5], l[0]));
+  const double c6_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
+  const double t6_0_0 = c6_0 + c6_y;
+  const double t6_0_1 = c6_0 - c6_y;
+  e[29] = t6_0_0;
+  e[31] = t6_0_0;
+  e[32] = t6_0_1;
+  e[30] = t6_0_1;
+  const double c7_0 = fma(double(9), l[5], l[0]);
+  const double c7_y = fma(double(27), l[11], mul_rn(double(3), l[2]));
+  const double t7_0_0 = c7_0 + c7_y;
+  const double t7_0_1 = c7_0 - c7_y;
+  e[35] = t7_0_0;
+  e[36] = t7_0_1;
+  const double c8_0 = l[0] + l[4];
+  const double c8_x = l[1] + l[10];
+  const double t8_0_0 = c8_0 + c8_x;
+  const double t8_0_1 = c8_0 - c8_x;
+  e[1] = t8_0_0;
+  e[2] = t8_0_1;
+  const double c9_0 = l[0] + l[4] + l[5] + l[6];
+  const double c9_x = fma(double(3), l[10], l[1]);
+  const double c9_y = fma(double(3), l[11], l[2]);
+  const double c9_xy = l[7];
+  const double t9_0_0 = c9_0 + c9_x;
+  const double t9_0_1 = c9_0 - c9_x;
+  const double t9_0_2 = c9_y + c9_xy;
+  const double t9_0_3 = c9_y - c9_xy;
+  const double t9_1_0 = t9_0_0 + t9_0_2;
+  const double t9_1_1 = t9_0_0 - t9_0_2;
+  const double t9_1_2 = t9_0_1 + t9_0_3;
+  const double t9_1_3 = t9_0_1 - t9_0_3;
+  e[7] = t9_1_0;
+  e[9] = t9_1_0;
+  e[11] = t9_1_1;
+  e[14] = t9_1_1;
+  e[13] = t9_1_2;
+  e[12] = t9_1_2;
+  e[10] = t9_1_3;
+  e[8] = t9_1_3;
+  const double c10_0 = fma(double(4), l[4], l[0]);
+  const double c10_x = fma(double(8), l[10], mul_rn(double(2), l[1]));
+  const double t10_0_0 = c10_0 + c10_x;
+  const double t10_0_1 = c10_0 - c10_x;
+  e[15] = t10_0_0;
+  e[16] = t10_0_1;
+  const double c11_0 = fma(double(4), l[6], fma(double(4), l[4], l[0]));
+  const double c11_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
+  const double t11_0_0 = c11_0 + c11_x;
+  const double t11_0_1 = c11_0 - c11_x;
+  e[25] = t11_0_0;
+  e[27] = t11_0_0;
+  e[28] = t11_0_1;
+  e[26] = t11_0_1;
+  const double c12_0 = fma(double(4), l[5], fma(double(4), l[4], l[0]));
+  const double c12_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
+  const double c12_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
+  const double c12_xy = mul_rn(double(4), l[7]);
+  const double t12_0_0 = c12_0 + c12_x;
+  const double t12_0_1 = c12_0 - c12_x;
+  const double t12_0_2 = c12_y + c12_xy;
+  const double t12_0_3 = c12_y - c12_xy;
+  const double t12_1_0 = t12_0_0 + t12_0_2;
+  const double t12_1_1 = t12_0_0 - t12_0_2;
+  const double t12_1_2 = t12_0_1 + t12_0_3;
+  const double t12_1_3 = t12_0_1 - t12_0_3;
+  e[21] = t12_1_0;
+  e[23] = t12_1_1;
+  e[24] = t12_1_2;
+  e[22] = t12_1_3;
+  const double c13_0 = fma(double(9), l[4], l[0]);
+  const double c13_x = fma(double(27), l[10], mul_rn(double(3), l[1]));
   const double t13_0_0 = c13_0 + c13_x;
   const double t13_0_1 = c13_0 - c13_x;
   e[33] = t13_0_0;
@@ -293,31 +400,31 @@ __device__ __forceinline__ void moments(const A& F, T (&s)[13], T (&J)[91]) {
   const T M301_0 = fma(T(16), h202_xz, h111_xz);
   const T M310_0 = fma(T(16), h220_xy, h111_xy);
   const T M400_0 = ((fma(T(16), h220_0, fma(T(16), h200_0, h100_0))) + (fma(T(81), h300_0, fma(T(16), h202_0, h111_0))));
-  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, T(27) * h003_z)));
-  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, T(16) * h022_y)));
-  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, T(8) * h200_x)));
-  const T M002_1 = ((fma(T(32), h202_0, fma(T(32), h022_0, fma(T(16), h002_0, h001_0)))) + (fma(T(3), h111_0, T(81) * h003_0)));
-  const T M011_1 = fma(T(3), h111_yz, T(32) * h022_yz);
-  const T M020_1 = ((fma(T(32), h220_0, fma(T(81), h030_0, fma(T(16), h020_0, h010_0)))) + (fma(T(3), h111_0, T(32) * h022_0)));
-  const T M101_1 = fma(T(32), h202_xz, T(3) * h111_xz);
-  const T M110_1 = fma(T(32), h220_xy, T(3) * h111_xy);
-  const T M200_1 = ((fma(T(81), h300_0, fma(T(32), h202_0, fma(T(3), h111_0, h100_0)))) + (fma(T(32), h220_0, T(16) * h200_0)));
-  const T M003_1 = ((fma(T(64), h202_z, fma(T(64), h022_z, fma(T(32), h002_z, h001_z)))) + (fma(T(3), h111_z, T(243) * h003_z)));
-  const T M012_1 = fma(T(3), h111_y, T(64) * h022_y);
-  const T M021_1 = fma(T(3), h111_z, T(64) * h022_z);
-  const T M030_1 = ((fma(T(64), h220_y, fma(T(243), h030_y, fma(T(32), h020_y, h010_y)))) + (fma(T(3), h111_y, T(64) * h022_y)));
-  const T M102_1 = fma(T(64), h202_x, T(3) * h111_x);
-  const T M111_1 = T(3) * h111_xyz;
-  const T M120_1 = fma(T(64), h220_x, T(3) * h111_x);
-  const T M201_1 = fma(T(64), h202_z, T(3) * h111_z);
-  const T M210_1 = fma(T(64), h220_y, T(3) * h111_y);
-  const T M300_1 = ((fma(T(243), h300_x, fma(T(64), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(64), h220_x, T(32) * h200_x)));
-  const T M002_2 = ((fma(T(256), h202_0, fma(T(256), h022_0, fma(T(64), h002_0, h001_0)))) + (fma(T(9), h111_0, T(729) * h003_0)));
-  const T M011_2 = fma(T(9), h111_yz, T(256) * h022_yz);
-  const T M020_2 = ((fma(T(256), h220_0, fma(T(729), h030_0, fma(T(64), h020_0, h010_0)))) + (fma(T(9), h111_0, T(256) * h022_0)));
-  const T M101_2 = fma(T(256), h202_xz, T(9) * h111_xz);
-  const T M110_2 = fma(T(256), h220_xy, T(9) * h111_xy);
-  const T M200_2 = ((fma(T(729), h300_0, fma(T(256), h202_0, fma(T(9), h111_0, h100_0)))) + (fma(T(256), h220_0, T(64) * h200_0)));
+  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, mul_rn(T(27), h003_z))));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(16), h022_y))));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, mul_rn(T(8), h200_x))));
+  const T M002_1 = ((fma(T(32), h202_0, fma(T(32), h022_0, fma(T(16), h002_0, h001_0)))) + (fma(T(3), h111_0, mul_rn(T(81), h003_0))));
+  const T M011_1 = fma(T(3), h111_yz, mul_rn(T(32), h022_yz));
+  const T M020_1 = ((fma(T(32), h220_0, fma(T(81), h030_0, fma(T(16), h020_0, h010_0)))) + (fma(T(3), h111_0, mul_rn(T(32), h022_0))));
+  const T M101_1 = fma(T(32), h202_xz, mul_rn(T(3), h111_xz));
+  const T M110_1 = fma(T(32), h220_xy, mul_rn(T(3), h111_xy));
+  const T M200_1 = ((fma(T(81), h300_0, fma(T(32), h202_0, fma(T(3), h111_0, h100_0)))) + (fma(T(32), h220_0, mul_rn(T(16), h200_0))));
+  const T M003_1 = ((fma(T(64), h202_z, fma(T(64), h022_z, fma(T(32), h002_z, h001_z)))) + (fma(T(3), h111_z, mul_rn(T(243), h003_z))));
+  const T M012_1 = fma(T(3), h111_y, mul_rn(T(64), h022_y));
+  const T M021_1 = fma(T(3), h111_z, mul_rn(T(64), h022_z));
+  const T M030_1 = ((fma(T(64), h220_y, fma(T(243), h030_y, fma(T(32), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(64), h022_y))));
+  const T M102_1 = fma(T(64), h202_x, mul_rn(T(3), h111_x));
+  const T M111_1 = mul_rn(T(3), h111_xyz);
+  const T M120_1 = fma(T(64), h220_x, mul_rn(T(3), h111_x));
+  const T M201_1 = fma(T(64), h202_z, mul_rn(T(3), h111_z));
+  const T M210_1 = fma(T(64), h220_y, mul_rn(T(3), h111_y));
+  const T M300_1 = ((fma(T(243), h300_x, fma(T(64), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(64), h220_x, mul_rn(T(32), h200_x))));
+  const T M002_2 = ((fma(T(256), h202_0, fma(T(256), h022_0, fma(T(64), h002_0, h001_0)))) + (fma(T(9), h111_0, mul_rn(T(729), h003_0))));
+  const T M011_2 = fma(T(9), h111_yz, mul_rn(T(256), h022_yz));
+  const T M020_2 = ((fma(T(256), h220_0, fma(T(729), h030_0, fma(T(64), h020_0, h010_0)))) + (fma(T(9), h111_0, mul_rn(T(256), h022_0))));
+  const T M101_2 = fma(T(256), h202_xz, mul_rn(T(9), h111_xz));
+  const T M110_2 = fma(T(256), h220_xy, mul_rn(T(9), h111_xy));
+  const T M200_2 = ((fma(T(729), h300_0, fma(T(256), h202_0, fma(T(9), h111_0, h100_0)))) + (fma(T(256), h220_0, mul_rn(T(64), h200_0))));
   s[0] = M000_0;
   s[1] = M100_0;
   s[2] = M010_0;
@@ -542,9 +649,9 @@ __device__ __forceinline__ void moments_s(const A& F, T (&s)[13]) {
   const T M101_0 = fma(T(4), h202_xz, h111_xz);
   const T M110_0 = fma(T(4), h220_xy, h111_xy);
   const T M200_0 = ((fma(T(4), h220_0, fma(T(4), h200_0, h100_0))) + (fma(T(9), h300_0, fma(T(4), h202_0, h111_0))));
-  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, T(27) * h003_z)));
-  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, T(16) * h022_y)));
-  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, T(8) * h200_x)));
+  const T M001_1 = ((fma(T(16), h202_z, fma(T(16), h022_z, fma(T(8), h002_z, h001_z)))) + (fma(T(3), h111_z, mul_rn(T(27), h003_z))));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(16), h022_y))));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, mul_rn(T(8), h200_x))));
   s[0] = M000_0;
   s[1] = M100_0;
   s[2] = M010_0;
@@ -558,6 +665,333 @@ __device__ __forceinline__ void moments_s(const A& F, T (&s)[13]) {
   s[10] = M100_1;
   s[11] = M010_1;
   s[12] = M001_1;
+}
+
+// z-mirror-symmetric F: s and J of the nine z-even basis functions (ZEVEN order).
+template <class T, class A>
+__device__ __forceinline__ void moments2d(const A& F, T (&s)[9], T (&J)[45]) {
+  const T h000_0 = F[0];
+  const T w1_0_0 = F[5] + F[6];
+  const T w1_0_1 = F[5] - F[6];
+  const T h001_0 = w1_0_0;
+  const T h001_z = w1_0_1;
+  const T w2_0_0 = F[19] + F[20];
+  const T w2_0_1 = F[19] - F[20];
+  const T h002_0 = w2_0_0;
+  const T h002_z = w2_0_1;
+  const T w3_0_0 = F[37] + F[38];
+  const T w3_0_1 = F[37] - F[38];
+  const T h003_0 = w3_0_0;
+  const T h003_z = w3_0_1;
+  const T w4_0_0 = F[3] + F[4];
+  const T w4_0_1 = F[3] - F[4];
+  const T h010_0 = w4_0_0;
+  const T h010_y = w4_0_1;
+  const T w5_0_0 = F[17] + F[18];
+  const T w5_0_1 = F[17] - F[18];
+  const T h020_0 = w5_0_0;
+  const T h020_y = w5_0_1;
+  const T w6_0_0 = F[29] + F[32];
+  const T w6_0_1 = F[29] - F[32];
+  const T w6_0_2 = F[31] + F[30];
+  const T w6_0_3 = F[31] - F[30];
+  const T w6_1_0 = w6_0_0 + w6_0_2;
+  const T w6_1_1 = w6_0_0 - w6_0_2;
+  const T w6_1_2 = w6_0_1 + w6_0_3;
+  const T w6_1_3 = w6_0_1 - w6_0_3;
+  const T h022_0 = w6_1_0;
+  const T h022_z = w6_1_1;
+  const T h022_y = w6_1_2;
+  const T h022_yz = w6_1_3;
+  const T w7_0_0 = F[35] + F[36];
+  const T w7_0_1 = F[35] - F[36];
+  const T h030_0 = w7_0_0;
+  const T h030_y = w7_0_1;
+  const T w8_0_0 = F[1] + F[2];
+  const T w8_0_1 = F[1] - F[2];
+  const T h100_0 = w8_0_0;
+  const T h100_x = w8_0_1;
+  const T w9_0_0 = F[7] + F[13];
+  const T w9_0_1 = F[7] - F[13];
+  const T w9_0_2 = F[9] + F[12];
+  const T w9_0_3 = F[9] - F[12];
+  const T w9_0_4 = F[11] + F[10];
+  const T w9_0_5 = F[11] - F[10];
+  const T w9_0_6 = F[14] + F[8];
+  const T w9_0_7 = F[14] - F[8];
+  const T w9_1_0 = w9_0_0 + w9_0_4;
+  const T w9_1_1 = w9_0_0 - w9_0_4;
+  const T w9_1_2 = w9_0_1 + w9_0_5;
+  const T w9_1_3 = w9_0_1 - w9_0_5;
+  const T w9_1_4 = w9_0_2 + w9_0_6;
+  const T w9_1_5 = w9_0_2 - w9_0_6;
+  const T w9_1_6 = w9_0_3 + w9_0_7;
+  const T w9_1_7 = w9_0_3 - w9_0_7;
+  const T w9_2_0 = w9_1_0 + w9_1_4;
+  const T w9_2_1 = w9_1_0 - w9_1_4;
+  const T w9_2_2 = w9_1_1 + w9_1_5;
+  const T w9_2_3 = w9_1_1 - w9_1_5;
+  const T w9_2_4 = w9_1_2 + w9_1_6;
+  const T w9_2_5 = w9_1_2 - w9_1_6;
+  const T w9_2_6 = w9_1_3 + w9_1_7;
+  const T w9_2_7 = w9_1_3 - w9_1_7;
+  const T h111_0 = w9_2_0;
+  const T h111_z = w9_2_1;
+  const T h111_y = w9_2_2;
+  const T h111_yz = w9_2_3;
+  const T h111_x = w9_2_4;
+  const T h111_xz = w9_2_5;
+  const T h111_xy = w9_2_6;
+  const T h111_xyz = w9_2_7;
+  const T w10_0_0 = F[15] + F[16];
+  const T w10_0_1 = F[15] - F[16];
+  const T h200_0 = w10_0_0;
+  const T h200_x = w10_0_1;
+  const T w11_0_0 = F[25] + F[28];
+  const T w11_0_1 = F[25] - F[28];
+  const T w11_0_2 = F[27] + F[26];
+  const T w11_0_3 = F[27] - F[26];
+  const T w11_1_0 = w11_0_0 + w11_0_2;
+  const T w11_1_1 = w11_0_0 - w11_0_2;
+  const T w11_1_2 = w11_0_1 + w11_0_3;
+  const T w11_1_3 = w11_0_1 - w11_0_3;
+  const T h202_0 = w11_1_0;
+  const T h202_z = w11_1_1;
+  const T h202_x = w11_1_2;
+  const T h202_xz = w11_1_3;
+  const T w12_0_0 = F[21] + F[24];
+  const T w12_0_1 = F[21] - F[24];
+  const T w12_0_2 = F[23] + F[22];
+  const T w12_0_3 = F[23] - F[22];
+  const T w12_1_0 = w12_0_0 + w12_0_2;
+  const T w12_1_1 = w12_0_0 - w12_0_2;
+  const T w12_1_2 = w12_0_1 + w12_0_3;
+  const T w12_1_3 = w12_0_1 - w12_0_3;
+  const T h220_0 = w12_1_0;
+  const T h220_y = w12_1_1;
+  const T h220_x = w12_1_2;
+  const T h220_xy = w12_1_3;
+  const T w13_0_0 = F[33] + F[34];
+  const T w13_0_1 = F[33] - F[34];
+  const T h300_0 = w13_0_0;
+  const T h300_x = w13_0_1;
+  const T M000_0 = (((h000_0 + h010_0 + h100_0 + h220_0) + (h001_0 + h020_0 + h111_0 + h300_0)) + ((h002_0 + h022_0 + h200_0) + (h003_0 + h030_0 + h202_0)));
+  const T M010_0 = ((fma(T(3), h030_y, fma(T(2), h020_y, h010_y))) + (fma(T(2), h220_y, fma(T(2), h022_y, h111_y))));
+  const T M100_0 = ((fma(T(2), h220_x, fma(T(2), h200_x, h100_x))) + (fma(T(3), h300_x, fma(T(2), h202_x, h111_x))));
+  const T M002_0 = ((fma(T(4), h022_0, fma(T(4), h002_0, h001_0))) + (fma(T(4), h202_0, fma(T(9), h003_0, h111_0))));
+  const T M020_0 = ((fma(T(9), h030_0, fma(T(4), h020_0, h010_0))) + (fma(T(4), h220_0, fma(T(4), h022_0, h111_0))));
+  const T M110_0 = fma(T(4), h220_xy, h111_xy);
+  const T M200_0 = ((fma(T(4), h220_0, fma(T(4), h200_0, h100_0))) + (fma(T(9), h300_0, fma(T(4), h202_0, h111_0))));
+  const T M012_0 = fma(T(8), h022_y, h111_y);
+  const T M030_0 = ((fma(T(27), h030_y, fma(T(8), h020_y, h010_y))) + (fma(T(8), h220_y, fma(T(8), h022_y, h111_y))));
+  const T M102_0 = fma(T(8), h202_x, h111_x);
+  const T M120_0 = fma(T(8), h220_x, h111_x);
+  const T M210_0 = fma(T(8), h220_y, h111_y);
+  const T M300_0 = ((fma(T(8), h220_x, fma(T(8), h200_x, h100_x))) + (fma(T(27), h300_x, fma(T(8), h202_x, h111_x))));
+  const T M004_0 = ((fma(T(16), h022_0, fma(T(16), h002_0, h001_0))) + (fma(T(16), h202_0, fma(T(81), h003_0, h111_0))));
+  const T M022_0 = fma(T(16), h022_0, h111_0);
+  const T M040_0 = ((fma(T(81), h030_0, fma(T(16), h020_0, h010_0))) + (fma(T(16), h220_0, fma(T(16), h022_0, h111_0))));
+  const T M112_0 = h111_xy;
+  const T M130_0 = fma(T(16), h220_xy, h111_xy);
+  const T M202_0 = fma(T(16), h202_0, h111_0);
+  const T M220_0 = fma(T(16), h220_0, h111_0);
+  const T M310_0 = fma(T(16), h220_xy, h111_xy);
+  const T M400_0 = ((fma(T(16), h220_0, fma(T(16), h200_0, h100_0))) + (fma(T(81), h300_0, fma(T(16), h202_0, h111_0))));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(16), h022_y))));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, mul_rn(T(8), h200_x))));
+  const T M020_1 = ((fma(T(32), h220_0, fma(T(81), h030_0, fma(T(16), h020_0, h010_0)))) + (fma(T(3), h111_0, mul_rn(T(32), h022_0))));
+  const T M110_1 = fma(T(32), h220_xy, mul_rn(T(3), h111_xy));
+  const T M200_1 = ((fma(T(81), h300_0, fma(T(32), h202_0, fma(T(3), h111_0, h100_0)))) + (fma(T(32), h220_0, mul_rn(T(16), h200_0))));
+  const T M012_1 = fma(T(3), h111_y, mul_rn(T(64), h022_y));
+  const T M030_1 = ((fma(T(64), h220_y, fma(T(243), h030_y, fma(T(32), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(64), h022_y))));
+  const T M102_1 = fma(T(64), h202_x, mul_rn(T(3), h111_x));
+  const T M120_1 = fma(T(64), h220_x, mul_rn(T(3), h111_x));
+  const T M210_1 = fma(T(64), h220_y, mul_rn(T(3), h111_y));
+  const T M300_1 = ((fma(T(243), h300_x, fma(T(64), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(64), h220_x, mul_rn(T(32), h200_x))));
+  const T M020_2 = ((fma(T(256), h220_0, fma(T(729), h030_0, fma(T(64), h020_0, h010_0)))) + (fma(T(9), h111_0, mul_rn(T(256), h022_0))));
+  const T M110_2 = fma(T(256), h220_xy, mul_rn(T(9), h111_xy));
+  const T M200_2 = ((fma(T(729), h300_0, fma(T(256), h202_0, fma(T(9), h111_0, h100_0)))) + (fma(T(256), h220_0, mul_rn(T(64), h200_0))));
+  s[0] = M000_0;
+  s[1] = M100_0;
+  s[2] = M010_0;
+  s[3] = M200_0;
+  s[4] = M020_0;
+  s[5] = M002_0;
+  s[6] = M110_0;
+  s[7] = M100_1;
+  s[8] = M010_1;
+  J[0] = M000_0;
+  J[1] = M100_0;
+  J[2] = M200_0;
+  J[3] = M010_0;
+  J[4] = M110_0;
+  J[5] = M020_0;
+  J[6] = M200_0;
+  J[7] = M300_0;
+  J[8] = M210_0;
+  J[9] = M400_0;
+  J[10] = M020_0;
+  J[11] = M120_0;
+  J[12] = M030_0;
+  J[13] = M220_0;
+  J[14] = M040_0;
+  J[15] = M002_0;
+  J[16] = M102_0;
+  J[17] = M012_0;
+  J[18] = M202_0;
+  J[19] = M022_0;
+  J[20] = M004_0;
+  J[21] = M110_0;
+  J[22] = M210_0;
+  J[23] = M120_0;
+  J[24] = M310_0;
+  J[25] = M130_0;
+  J[26] = M112_0;
+  J[27] = M220_0;
+  J[28] = M100_1;
+  J[29] = M200_1;
+  J[30] = M110_1;
+  J[31] = M300_1;
+  J[32] = M120_1;
+  J[33] = M102_1;
+  J[34] = M210_1;
+  J[35] = M200_2;
+  J[36] = M010_1;
+  J[37] = M110_1;
+  J[38] = M020_1;
+  J[39] = M210_1;
+  J[40] = M030_1;
+  J[41] = M012_1;
+  J[42] = M120_1;
+  J[43] = M110_2;
+  J[44] = M020_2;
+}
+
+template <class T, class A>
+__device__ __forceinline__ void moments_s2d(const A& F, T (&s)[9]) {
+  const T h000_0 = F[0];
+  const T w1_0_0 = F[5] + F[6];
+  const T w1_0_1 = F[5] - F[6];
+  const T h001_0 = w1_0_0;
+  const T h001_z = w1_0_1;
+  const T w2_0_0 = F[19] + F[20];
+  const T w2_0_1 = F[19] - F[20];
+  const T h002_0 = w2_0_0;
+  const T h002_z = w2_0_1;
+  const T w3_0_0 = F[37] + F[38];
+  const T w3_0_1 = F[37] - F[38];
+  const T h003_0 = w3_0_0;
+  const T h003_z = w3_0_1;
+  const T w4_0_0 = F[3] + F[4];
+  const T w4_0_1 = F[3] - F[4];
+  const T h010_0 = w4_0_0;
+  const T h010_y = w4_0_1;
+  const T w5_0_0 = F[17] + F[18];
+  const T w5_0_1 = F[17] - F[18];
+  const T h020_0 = w5_0_0;
+  const T h020_y = w5_0_1;
+  const T w6_0_0 = F[29] + F[32];
+  const T w6_0_1 = F[29] - F[32];
+  const T w6_0_2 = F[31] + F[30];
+  const T w6_0_3 = F[31] - F[30];
+  const T w6_1_0 = w6_0_0 + w6_0_2;
+  const T w6_1_1 = w6_0_0 - w6_0_2;
+  const T w6_1_2 = w6_0_1 + w6_0_3;
+  const T w6_1_3 = w6_0_1 - w6_0_3;
+  const T h022_0 = w6_1_0;
+  const T h022_z = w6_1_1;
+  const T h022_y = w6_1_2;
+  const T h022_yz = w6_1_3;
+  const T w7_0_0 = F[35] + F[36];
+  const T w7_0_1 = F[35] - F[36];
+  const T h030_0 = w7_0_0;
+  const T h030_y = w7_0_1;
+  const T w8_0_0 = F[1] + F[2];
+  const T w8_0_1 = F[1] - F[2];
+  const T h100_0 = w8_0_0;
+  const T h100_x = w8_0_1;
+  const T w9_0_0 = F[7] + F[13];
+  const T w9_0_1 = F[7] - F[13];
+  const T w9_0_2 = F[9] + F[12];
+  const T w9_0_3 = F[9] - F[12];
+  const T w9_0_4 = F[11] + F[10];
+  const T w9_0_5 = F[11] - F[10];
+  const T w9_0_6 = F[14] + F[8];
+  const T w9_0_7 = F[14] - F[8];
+  const T w9_1_0 = w9_0_0 + w9_0_4;
+  const T w9_1_1 = w9_0_0 - w9_0_4;
+  const T w9_1_2 = w9_0_1 + w9_0_5;
+  const T w9_1_3 = w9_0_1 - w9_0_5;
+  const T w9_1_4 = w9_0_2 + w9_0_6;
+  const T w9_1_5 = w9_0_2 - w9_0_6;
+  const T w9_1_6 = w9_0_3 + w9_0_7;
+  const T w9_1_7 = w9_0_3 - w9_0_7;
+  const T w9_2_0 = w9_1_0 + w9_1_4;
+  const T w9_2_1 = w9_1_0 - w9_1_4;
+  const T w9_2_2 = w9_1_1 + w9_1_5;
+  const T w9_2_3 = w9_1_1 - w9_1_5;
+  const T w9_2_4 = w9_1_2 + w9_1_6;
+  const T w9_2_5 = w9_1_2 - w9_1_6;
+  const T w9_2_6 = w9_1_3 + w9_1_7;
+  const T w9_2_7 = w9_1_3 - w9_1_7;
+  const T h111_0 = w9_2_0;
+  const T h111_z = w9_2_1;
+  const T h111_y = w9_2_2;
+  const T h111_yz = w9_2_3;
+  const T h111_x = w9_2_4;
+  const T h111_xz = w9_2_5;
+  const T h111_xy = w9_2_6;
+  const T h111_xyz = w9_2_7;
+  const T w10_0_0 = F[15] + F[16];
+  const T w10_0_1 = F[15] - F[16];
+  const T h200_0 = w10_0_0;
+  const T h200_x = w10_0_1;
+  const T w11_0_0 = F[25] + F[28];
+  const T w11_0_1 = F[25] - F[28];
+  const T w11_0_2 = F[27] + F[26];
+  const T w11_0_3 = F[27] - F[26];
+  const T w11_1_0 = w11_0_0 + w11_0_2;
+  const T w11_1_1 = w11_0_0 - w11_0_2;
+  const T w11_1_2 = w11_0_1 + w11_0_3;
+  const T w11_1_3 = w11_0_1 - w11_0_3;
+  const T h202_0 = w11_1_0;
+  const T h202_z = w11_1_1;
+  const T h202_x = w11_1_2;
+  const T h202_xz = w11_1_3;
+  const T w12_0_0 = F[21] + F[24];
+  const T w12_0_1 = F[21] - F[24];
+  const T w12_0_2 = F[23] + F[22];
+  const T w12_0_3 = F[23] - F[22];
+  const T w12_1_0 = w12_0_0 + w12_0_2;
+  const T w12_1_1 = w12_0_0 - w12_0_2;
+  const T w12_1_2 = w12_0_1 + w12_0_3;
+  const T w12_1_3 = w12_0_1 - w12_0_3;
+  const T h220_0 = w12_1_0;
+  const T h220_y = w12_1_1;
+  const T h220_x = w12_1_2;
+  const T h220_xy = w12_1_3;
+  const T w13_0_0 = F[33] + F[34];
+  const T w13_0_1 = F[33] - F[34];
+  const T h300_0 = w13_0_0;
+  const T h300_x = w13_0_1;
+  const T M000_0 = (((h000_0 + h010_0 + h100_0 + h220_0) + (h001_0 + h020_0 + h111_0 + h300_0)) + ((h002_0 + h022_0 + h200_0) + (h003_0 + h030_0 + h202_0)));
+  const T M010_0 = ((fma(T(3), h030_y, fma(T(2), h020_y, h010_y))) + (fma(T(2), h220_y, fma(T(2), h022_y, h111_y))));
+  const T M100_0 = ((fma(T(2), h220_x, fma(T(2), h200_x, h100_x))) + (fma(T(3), h300_x, fma(T(2), h202_x, h111_x))));
+  const T M002_0 = ((fma(T(4), h022_0, fma(T(4), h002_0, h001_0))) + (fma(T(4), h202_0, fma(T(9), h003_0, h111_0))));
+  const T M020_0 = ((fma(T(9), h030_0, fma(T(4), h020_0, h010_0))) + (fma(T(4), h220_0, fma(T(4), h022_0, h111_0))));
+  const T M110_0 = fma(T(4), h220_xy, h111_xy);
+  const T M200_0 = ((fma(T(4), h220_0, fma(T(4), h200_0, h100_0))) + (fma(T(9), h300_0, fma(T(4), h202_0, h111_0))));
+  const T M010_1 = ((fma(T(16), h220_y, fma(T(27), h030_y, fma(T(8), h020_y, h010_y)))) + (fma(T(3), h111_y, mul_rn(T(16), h022_y))));
+  const T M100_1 = ((fma(T(27), h300_x, fma(T(16), h202_x, fma(T(3), h111_x, h100_x)))) + (fma(T(16), h220_x, mul_rn(T(8), h200_x))));
+  s[0] = M000_0;
+  s[1] = M100_0;
+  s[2] = M010_0;
+  s[3] = M200_0;
+  s[4] = M020_0;
+  s[5] = M002_0;
+  s[6] = M110_0;
+  s[7] = M100_1;
+  s[8] = M010_1;
 }
 
 // rho = sum f, j = sum f xi, e2f = sum f |xi|^2 (Sec. 3, macroscopic step).
@@ -592,7 +1026,7 @@ __device__ __forceinline__ void f_moments(const A& f, T& rho, T& jx, T& jy, T& j
   const T sh4 = ((ps15 + ps17) + ps19);
   const T sh8 = (((ps21 + ps23) + ps25) + ((ps27 + ps29) + ps31));
   const T sh9 = ((ps33 + ps35) + ps37);
-  e2f = ((fma(T(8), sh8, fma(T(3), sh3, sh1))) + (fma(T(9), sh9, T(4) * sh4)));
+  e2f = ((fma(T(8), sh8, fma(T(3), sh3, sh1))) + (fma(T(9), sh9, mul_rn(T(4), sh4))));
 }
 
 // sum g (the second population's share of the total energy).

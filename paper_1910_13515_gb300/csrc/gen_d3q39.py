@@ -142,7 +142,9 @@ def lincomb_chain(terms, T):
     elif c == -1:
         e = f"-{v}"
     else:
-        e = f"T({c}) * {v}".replace("T(", f"{T}(")
+        # a product that the compiler may not fuse into a later add: the rounding of every
+        # sum is then fixed by this text, whatever other uses of the product remain
+        e = f"mul_rn({T}({c}), {v})"
     for c, v in terms[1:]:
         if c == 1:
             e = f"{e} + {v}"
@@ -184,6 +186,14 @@ def gen_fold(em, T):
 GBASIS = [((0, 0, 0), 0), ((1, 0, 0), 0), ((0, 1, 0), 0), ((0, 0, 1), 0), ((2, 0, 0), 0),
           ((0, 2, 0), 0), ((0, 0, 2), 0), ((1, 1, 0), 0), ((1, 0, 1), 0), ((0, 1, 1), 0),
           ((1, 0, 0), 1), ((0, 1, 0), 1), ((0, 0, 1), 1)]
+
+
+# basis functions even in xi_z: on a lattice one cell thick in z whose populations are
+# mirror-symmetric in z (u_z = 0), the other four multipliers stay exactly zero and their
+# rows of J are exact zeros off the diagonal block, so the solve reduces to these nine.
+ZEVEN = [k for k in range(NM) if GBASIS[k][0][2] % 2 == 0]
+assert ZEVEN == [0, 1, 2, 4, 5, 6, 7, 10, 11]
+N2 = len(ZEVEN)
 
 
 def monomial_moment_terms(p, m=0):
@@ -241,15 +251,55 @@ def gen_moments():
             continue
         only.append(ln)
     only.append("}")
-    return em.lines + only, len(monos)
+    # z-mirror variants (9 z-even basis functions): the same fold and the same monomial
+    # expressions, restricted to what the z-even s and J need (the rest is dead code)
+    def two_d(signature, with_J):
+        out = ["", signature]
+        keep2 = {names[GBASIS[k]] for k in ZEVEN}
+        if with_J:
+            for a, k in enumerate(ZEVEN):
+                for b, l in enumerate(ZEVEN[:a + 1]):
+                    pk, mk = GBASIS[k]
+                    pl, ml = GBASIS[l]
+                    keep2.add(names[(tuple(x + y for x, y in zip(pk, pl)), mk + ml)])
+        for ln in body_s[4:]:
+            if ln.lstrip().startswith("s["):
+                continue
+            if ln.lstrip().startswith("const T M") and ln.split()[2] not in keep2:
+                continue
+            out.append(ln)
+        for a, k in enumerate(ZEVEN):
+            out.append(f"  s[{a}] = {names[GBASIS[k]]};")
+        if with_J:
+            for a, k in enumerate(ZEVEN):
+                for b, l in enumerate(ZEVEN[:a + 1]):
+                    pk, mk = GBASIS[k]
+                    pl, ml = GBASIS[l]
+                    out.append(f"  J[{tri(a, b)}] = "
+                               f"{names[(tuple(x + y for x, y in zip(pk, pl)), mk + ml)]};")
+        out.append("}")
+        return out
+    d2 = (["", "// z-mirror-symmetric F: s and J of the nine z-even basis functions (ZEVEN order)."]
+          + ["template <class T, class A>"]
+          + two_d("__device__ __forceinline__ void moments2d(const A& F, T (&s)[9], T (&J)[45]) {",
+                  True)[1:]
+          + ["", "template <class T, class A>"]
+          + two_d("__device__ __forceinline__ void moments_s2d(const A& F, T (&s)[9]) {",
+                  False)[1:])
+    return em.lines + only + d2, len(monos)
 
 
-def gen_exponents():
+def gen_exponents(zsym=False):
     """e_i = sum_k l_k phi_k(xi_i) for the 39 velocities, per orbit: the coefficients c_T of
-    the sign monomials, then the inverse butterflies."""
+    the sign monomials, then the inverse butterflies.  zsym: the z-odd multipliers are zero
+    (not read); z-mirrored velocities get the same exponent expression."""
     em = Emitter()
-    em("// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium).")
-    em("__device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]) {")
+    if zsym:
+        em("// The same with the z-odd multipliers zero (lattice one cell thick in z, u_z = 0).")
+        em("__device__ __forceinline__ void exponents2d(const double (&l)[13], double (&e)[39]) {")
+    else:
+        em("// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium).")
+        em("__device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]) {")
     for o, (key, axes, members) in enumerate(ORBITS):
         n = len(axes)
         # c_T = sum_k l_k * (coefficient of prod_{a in T} s_a in phi_k on this orbit)
@@ -257,6 +307,8 @@ def gen_exponents():
         for Tset in subsets(axes):
             terms = []
             for k in range(NM):
+                if zsym and k not in ZEVEN:
+                    continue
                 coef = 0
                 for p, c in BASIS[k].items():
                     if any(p[a] != 0 and key[a] == 0 for a in range(3)):
@@ -374,6 +426,7 @@ def selfcheck(lines):
     G = [rnd.uniform(0.1, 1.0) for _ in range(Q)]
     lam = [rnd.uniform(-1, 1) for _ in range(NM)]
     env = {"F": F, "f": F, "g": G, "l": lam, "fma": lambda a, b, c: a * b + c,
+           "mul_rn": lambda a, b: a * b,
            "T": float, "double": float, "s": [0.0] * NM, "J": [0.0] * 91, "e": [0.0] * Q}
     for ln in lines:
         t = ln.strip()
@@ -411,11 +464,95 @@ def selfcheck(lines):
     assert abs(env["gs"] - sum(G)) < 1e-12
 
 
+def strip_2d(lines):
+    """The lines without the z-mirror functions (they reuse variable names)."""
+    out, skip = [], False
+    for ln in lines:
+        if ln.startswith("__device__ __forceinline__ void exponents2d") or \
+                ln.startswith("__device__ __forceinline__ void moments2d") or \
+                ln.startswith("__device__ __forceinline__ void moments_s2d"):
+            skip = True
+        if not skip:
+            out.append(ln)
+        elif ln == "}":
+            skip = False
+    return out
+
+
+def function_body(lines, start):
+    out, on = [], False
+    for ln in lines:
+        if ln.startswith(start):
+            on = True
+            continue
+        if on:
+            if ln == "}":
+                break
+            out.append(ln)
+    return out
+
+
+def selfcheck_2d(lines):
+    """The z-mirror functions on z-symmetric inputs against direct sums over the 39."""
+    import random
+    import re
+    rnd = random.Random(11)
+    mirror = {i: VEL.index((VEL[i][0], VEL[i][1], -VEL[i][2])) for i in range(Q)}
+    F = [0.0] * Q
+    for i in range(Q):
+        if VEL[i][2] >= 0:
+            F[i] = F[mirror[i]] = rnd.uniform(0.1, 1.0)
+    lam = [rnd.uniform(-1, 1) if k in ZEVEN else 0.0 for k in range(NM)]
+    env = {"F": F, "l": lam, "fma": lambda a, b, c: a * b + c, "mul_rn": lambda a, b: a * b,
+           "T": float, "double": float,
+           "s": [0.0] * N2, "J": [0.0] * (N2 * (N2 + 1) // 2), "e": [0.0] * Q}
+
+    def run(body):
+        for ln in body:
+            t = ln.strip()
+            m = re.match(r"^(?:const\s+)?(?:T|double)\s+(.*);$", t)
+            if m:
+                for part in re.split(r",\s*(?=\w+\s*=)", m.group(1)):
+                    name, expr = part.split("=", 1)
+                    env[name.strip()] = eval(expr, env)
+                continue
+            m = re.match(r"^(\w+)\[(\d+)\]\s*=\s*(.*);$", t)
+            if m:
+                env[m.group(1)][int(m.group(2))] = eval(m.group(3), env)
+    run(function_body(lines, "__device__ __forceinline__ void exponents2d"))
+    for i in range(Q):
+        ref = sum(lam[k] * phi(k, VEL[i]) for k in range(NM))
+        assert abs(env["e"][i] - ref) < 1e-12, ("exponent2d", i)
+    run(function_body(lines, "__device__ __forceinline__ void moments2d"))
+    for a, k in enumerate(ZEVEN):
+        ref = sum(F[i] * phi(k, VEL[i]) for i in range(Q))
+        assert abs(env["s"][a] - ref) < 1e-11, ("s2d", k)
+        for b, l in enumerate(ZEVEN[:a + 1]):
+            ref = sum(F[i] * phi(k, VEL[i]) * phi(l, VEL[i]) for i in range(Q))
+            assert abs(env["J"][tri(a, b)] - ref) < 1e-9 * max(1, abs(ref)), ("J2d", k, l)
+    env["s"] = [0.0] * N2
+    run(function_body(lines, "__device__ __forceinline__ void moments_s2d"))
+    for a, k in enumerate(ZEVEN):
+        ref = sum(F[i] * phi(k, VEL[i]) for i in range(Q))
+        assert abs(env["s"][a] - ref) < 1e-11, ("s_2d", k)
+    # the z-odd sums vanish exactly on z-symmetric F (which the reduction relies on)
+    for k in range(NM):
+        if k not in ZEVEN:
+            assert sum(F[i] * phi(k, VEL[i]) for i in range(Q)) == 0.0
+
+
 def main():
     inv, L_hi, L_lo, table = exp_constants()
     lines = ["// d3q39_gen.cuh -- GENERATED by gen_d3q39.py; do not edit.",
-             "#pragma once", "", "namespace lbm39 {", "namespace gen {", ""]
+             "#pragma once", "", "namespace lbm39 {", "namespace gen {", "",
+             "// Rounded products that are never contracted into a fused multiply-add.",
+             "__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }",
+             "__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }",
+             ""]
     lines += gen_exponents()
+    lines.append("")
+    exp2d = gen_exponents(zsym=True)
+    lines += exp2d
     lines.append("")
     ml, nmono = gen_moments()
     lines += ml
@@ -433,7 +570,8 @@ def main():
         lines.append("    " + ", ".join(repr(t) for t in table[j:j + 4]) + ",")
     lines.append("};")
     lines += ["", "}  // namespace gen", "}  // namespace lbm39", ""]
-    selfcheck(lines)
+    selfcheck(strip_2d(lines))
+    selfcheck_2d(lines)
     out = os.path.join(HERE, "d3q39_gen.cuh")
     with open(out, "w") as fh:
         fh.write("\n".join(lines))

@@ -39,12 +39,16 @@ struct Desc {
   double mref[5];                     // sum of href: rho, j, sum f|xi|^2 + sum g
   long long N, Np;                    // cells, plane stride in elements
   long long t;                        // time step being taken (schedules fallback retries)
+  int d2;                             // one cell thick in z, z-mirror-symmetric populations
   int nx, ny, nz;
   int per[3];                         // periodic axes
   Phys ph;
 };
 
 enum { CTR_FAILED = 0, CTR_UPDATES = 1, CTR_HIST = 2, CTR_EPS = 34, CTR_N = 38 };
+// Set by lbm39_init when some fluid cell starts with u_z != 0 (outside the
+// block counters: not reported by lbm39_stats).
+constexpr int CTR_ASYM = 40;
 
 struct Coord {
   int x, y, z;
@@ -328,7 +332,9 @@ __device__ __noinline__ void fallback_cell(const double* state, long long Np, lo
 
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
-template <bool ODD, class P, int BLK>
+// D2: the nine-function constraint system of a z-mirror-symmetric lattice one
+// cell thick in z (Sys<true>; the same values as the full system).
+template <bool ODD, class P, int BLK, bool D2 = false>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
@@ -342,7 +348,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   // unless its embedding already meets the 13 constraints)
   const int maxit =
       !marked ? d.ph.maxit : (((d.t + (cell >> 5)) & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0);
-  const NewtonResult nr = newton<BLK, (sizeof(P) == 4)>(w, d.ph, maxit, true);
+  const NewtonResult nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
@@ -354,7 +360,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
 }
 
 // One time step over every fluid cell (even or odd AA pass).
-template <bool ODD, class P, int BLK>
+template <bool ODD, class P, int BLK, bool D2>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
   if (cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID))
-    step_cell<ODD, P, BLK>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
+    step_cell<ODD, P, BLK, D2>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 
@@ -387,11 +393,13 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
   const long long r = (long long)blockIdx.x * BLK + threadIdx.x;
   const long long cell = c0 + r;
   P* pop = static_cast<P*>(d.pop);
+  int asym = 0;
   if (r < len && cell < d.N) {
     const bool fluid = d.mask == nullptr || d.mask[cell] == MASK_FLUID;
     WS<BLK> w{smem + threadIdx.x};
     if (fluid) {
       const double rr = rho[r], ux = u[r], uy = u[us + r], uz = u[2 * us + r], TT = T[r];
+      asym = uz != 0.0;
       WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
       targets<BLK>(ux, uy, uz, TT, m);
       gaussian_guess<BLK>(ux, uy, uz, TT, lam);
@@ -409,6 +417,7 @@ __global__ void __launch_bounds__(BLK) k_init(Desc d, const double* rho, const d
       for (int k = 0; k < SOLVER_PLANES; ++k) d.lam[k * d.Np + cell] = 0.0;
     }
   }
+  if (__syncthreads_or(asym) && threadIdx.x == 0) atomicAdd(d.ctr + CTR_ASYM, 1ull);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 

@@ -64,6 +64,7 @@ bool params_ok(const lbm39_params* p) {
       p->init_maxit < 1 || p->init_maxit > 10000)
     return false;
   if (p->precision != LBM39_FP64 && p->precision != LBM39_MIXED) return false;
+  if (p->reduce_2d != 0 && p->reduce_2d != 1) return false;
   if (p->precision == LBM39_MIXED && !(p->ref_rho > 0.0 && p->ref_T > 0.0)) return false;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? p->nx : a == 1 ? p->ny : p->nz;
@@ -107,11 +108,15 @@ struct Launch {
     L->desc.t = L->t;
     const unsigned grid = (unsigned)((L->N + BLK - 1) / BLK);
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
+    // the reduced (z-mirror) system serves the FP64 path only (see reduction_allowed)
+    constexpr bool fp64 = sizeof(P) == 8;
     if (!odd) {
-      k_step<false, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (fp64 && L->desc.d2) k_step<false, P, BLK, fp64><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      else k_step<false, P, BLK, false><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
       if (L->fills) k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
     } else {
-      k_step<true, P, BLK><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      if (fp64 && L->desc.d2) k_step<true, P, BLK, fp64><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
+      else k_step<true, P, BLK, false><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
       if (L->fills) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
     }
   }
@@ -154,6 +159,7 @@ void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->precision = LBM39_FP64;
   p->ref_rho = 1.0; p->ref_T = 0.5;
   p->rho_inf = 1.0; p->T_inf = 0.5;
+  p->reduce_2d = 1;
 }
 
 int lbm39_velocities(int32_t* vel, double* w) {
@@ -361,11 +367,32 @@ static int init_begin(lbm39_lattice* L) {
   return LBM39_OK;
 }
 
+// Whether the z-mirror reduction holds: one cell thick in z, far field and
+// every initial u_z zero (the init kernel counted cells with u_z != 0), FP64
+// path.  The precision form keeps the full system: its FP32 factorisation also
+// forms the z-odd pivots and may reject a direction over one of them, which
+// the reduced system would not, so the two would not give the same values.
+static bool reduction_allowed(const lbm39_lattice* L) {
+  return L->p.reduce_2d == 1 && L->p.nz == 1 && L->p.u_inf[2] == 0.0 && !L->mixed;
+}
+
+// After the init kernels: waits for them and fixes the constraint system.
+static int init_end(lbm39_lattice* L) {
+  unsigned long long asym = 0;
+  CUDA_OK(cudaMemcpyAsync(&asym, L->ctr() + CTR_ASYM, sizeof asym, cudaMemcpyDeviceToHost,
+                          L->stream));
+  CUDA_OK(cudaStreamSynchronize(L->stream));
+  L->desc.d2 = reduction_allowed(L) && asym == 0 ? 1 : 0;
+  return LBM39_OK;
+}
+
 int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
   if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
   int rc = init_begin(L);
   if (rc) return rc;
-  return init_range(L, rho, u, L->N, T, 0, L->N);
+  rc = init_range(L, rho, u, L->N, T, 0, L->N);
+  if (rc) return rc;
+  return init_end(L);
 }
 
 int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
@@ -380,8 +407,7 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
     rc = init_range(L, static_cast<const double*>(drho), static_cast<const double*>(du), L->N,
                     static_cast<const double*>(dT), 0, L->N);
     if (rc) return rc;
-    CUDA_OK(cudaStreamSynchronize(L->stream));
-    return LBM39_OK;
+    return init_end(L);
   }
   const long long C = std::min(L->N, STAGE_CELLS);
   double* s = L->stage();
@@ -395,8 +421,7 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
     rc = init_range(L, s, s + C, C, s + 4 * C, c0, n);
     if (rc) return rc;
   }
-  CUDA_OK(cudaStreamSynchronize(L->stream));
-  return LBM39_OK;
+  return init_end(L);
 }
 
 int lbm39_step(lbm39_lattice* L, int64_t nsteps) {
@@ -527,6 +552,7 @@ int lbm39_save(lbm39_lattice* L, void* buf) {
   hdr[1] = (uint64_t)L->t;
   hdr[2] = (uint64_t)L->N;
   hdr[3] = (uint64_t)L->p.precision;
+  hdr[4] = (uint64_t)L->desc.d2;
   char* b = static_cast<char*>(buf);
   const size_t pb = L->pop_bytes(), lb = sizeof(double) * SOLVER_PLANES * L->Np;
   CUDA_OK(cudaMemcpyAsync(b, hdr, sizeof hdr, cudaMemcpyDefault, L->stream));
@@ -550,6 +576,7 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   CUDA_OK(cudaMemsetAsync(L->ctr(), 0, sizeof(unsigned long long) * 64, L->stream));
   CUDA_OK(cudaStreamSynchronize(L->stream));
   L->t = (long long)hdr[1];
+  L->desc.d2 = hdr[4] == 1 && reduction_allowed(L) ? 1 : 0;
   L->initialized = true;
   return LBM39_OK;
 }

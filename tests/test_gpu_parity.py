@@ -190,6 +190,41 @@ def test_host_io_pinned_and_pageable_paths_agree(Lat):
         assert np.array_equal(x, y) and np.array_equal(x, z)
 
 
+def _ckpt_mode(buf):
+    return int(buf[:256].view(torch.int64)[4].item())
+
+
+def test_z_mirror_reduction_changes_no_value(Lat):
+    """On a lattice one cell thick in z with u_z = 0 the FP64 path solves the nine z-even
+    constraints only (the others are exact zeros there): the state after 60 steps -- populations,
+    multipliers and cached equilibria -- and the Newton and sensor counts are bit for bit those of
+    the full 13-constraint solve (reduce_2d = 0), on the airfoil lattice (bounce-back, freestream,
+    outflow).  The precision form keeps the full system."""
+    s = inputs.naca(nx=96, ny=48, chord=24, x_le=24)
+    La = Lat.from_setup(s)
+    Lb = Lat.from_setup(s, reduce_2d=0)
+    for L in (La, Lb):
+        L.step(60)
+        assert L.sync() == 0
+    ba, bb = La.checkpoint(), Lb.checkpoint()
+    assert _ckpt_mode(ba) == 1 and _ckpt_mode(bb) == 0
+    assert torch.equal(ba[256:], bb[256:])
+    sa, sb = La.stats(), Lb.stats()
+    assert list(sa.newton_hist) == list(sb.newton_hist)
+    assert list(sa.eps_hist) == list(sb.eps_hist)
+    Lm = Lat.from_setup(s, precision=1)
+    assert _ckpt_mode(Lm.checkpoint()) == 0
+
+
+def test_one_cell_thick_lattice_with_u_z_keeps_the_full_solve(Lat):
+    """nz = 1 with u_z != 0 breaks the mirror symmetry: the full system runs (mode 0), at parity
+    with the oracle."""
+    s = inputs.box(seed=8, shape=(1, 14, 18))
+    assert np.abs(s.u[2]).max() > 0.01
+    L, st = assert_parity(Lat, s, 60)
+    assert _ckpt_mode(L.checkpoint()) == 0
+
+
 def outside_blob_box():
     """Periodic 12x10x8 box at a realizable state (u = (1, 0.2, 0), T = 0.5) with an 18-cell
     blob at a state outside the 13-moment cone: u = (1.416, -0.348, 0), T = 0.414, rho = 0.954,
