@@ -660,8 +660,14 @@ __global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict
   const long long cell = tl.cell0 + threadIdx.x;
   if (cell < sd.N && (sd.mask == nullptr || sd.mask[cell] == MASK_FLUID)) {
     WS<BLK> w{smem + threadIdx.x};
-    if (t & 1) step_cell<true, P, BLK>(sd, cell, w, s_ctr);
-    else step_cell<false, P, BLK>(sd, cell, w, s_ctr);
+    // the lattice's constraint system (the z-mirror reduction serves FP64 lattices only)
+    if (sizeof(P) == 8 && sd.d2) {
+      if (t & 1) step_cell<true, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
+      else step_cell<false, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
+    } else {
+      if (t & 1) step_cell<true, P, BLK>(sd, cell, w, s_ctr);
+      else step_cell<false, P, BLK>(sd, cell, w, s_ctr);
+    }
   }
   flush_stats<BLK>(s_ctr, sd.ctr);
 }
