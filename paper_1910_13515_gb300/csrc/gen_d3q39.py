@@ -541,7 +541,8 @@ def selfcheck_2d(lines):
             assert sum(F[i] * phi(k, VEL[i]) for i in range(Q)) == 0.0
 
 
-def main():
+def generate():
+    """The lines of d3q39_gen.cuh, after the self-checks."""
     inv, L_hi, L_lo, table = exp_constants()
     lines = ["// d3q39_gen.cuh -- GENERATED by gen_d3q39.py; do not edit.",
              "#pragma once", "", "namespace lbm39 {", "namespace gen {", "",
@@ -572,6 +573,11 @@ def main():
     lines += ["", "}  // namespace gen", "}  // namespace lbm39", ""]
     selfcheck(strip_2d(lines))
     selfcheck_2d(lines)
+    return lines, nmono
+
+
+def main():
+    lines, nmono = generate()
     out = os.path.join(HERE, "d3q39_gen.cuh")
     with open(out, "w") as fh:
         fh.write("\n".join(lines))
