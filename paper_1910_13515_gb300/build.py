@@ -1,6 +1,6 @@
 """Build the CUDA library liblbm39.so (sm_103a) in-tree with nvcc.
 
-One translation unit per precision form, compiled in parallel, then linked.
+One translation unit (lbm39.cu with its headers), then linked into the shared library.
 """
 from __future__ import annotations
 

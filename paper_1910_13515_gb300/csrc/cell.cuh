@@ -202,7 +202,7 @@ __device__ __forceinline__ double sum_sq(const double (&v)[N]) {
   return s;
 }
 
-// In-place LDL^T of a packed symmetric 13x13 J (unit-lower L below a diagonal
+// In-place LDL^T of a packed symmetric N x N J (unit-lower L below a diagonal
 // D) and the solve J x = b (b overwritten by x).  False if a pivot is not
 // positive (J not numerically SPD).
 template <class T, int N = NM>
@@ -296,7 +296,8 @@ struct NewtonResult {
   int failed;
 };
 
-// Newton-Raphson for the 13 multipliers (Sec. 3, Sec. 5 step table), from the
+// Newton-Raphson for the multipliers (Sec. 3, Sec. 5 step table; all 13, or
+// with D2 the nine z-even ones, the others staying exactly zero), from the
 // multipliers in `lam` (warm start or Gaussian cold start).  Reading of the
 // stopping rule: stop when max|G| < tol, after at least min_upd updates,
 // except that a solve landing in [tol/100, tol) takes one more full

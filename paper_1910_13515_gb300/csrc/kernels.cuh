@@ -11,12 +11,13 @@
 // gathers h_i(x) = h*_i(x - xi_i) from slot (x - xi_i, opp i), collides and
 // pushes h*_i(x) into slot (x + xi_i, i), which is the pre-collision h_i of
 // the next time step.  Every slot is read and written by one thread only (the
-// slot pushed for direction i is the one gathered for opp(i)).  Half-way
-// bounce-back: a source (odd gather) or destination (odd push) that is solid
-// redirects to the cell's own slot of the opposite direction; the per-cell
-// bit set Desc::bounce marks the directions whose source is solid.
-// Freestream and outflow cells never collide; the fill kernels give the
-// fluid cells what those cells would have streamed (Sec. 4 boundary kinds).
+// slot pushed for direction i is the one gathered for opp(i)).  Solid,
+// freestream and outflow cells never collide.  After each pass the fill
+// kernels write into the slots of those cells (and, after an odd pass, of
+// their fluid neighbours) what the fluid cells read next: the half-way
+// bounce-back copies of solid cells and what freestream and outflow cells
+// would have streamed (Sec. 4 boundary kinds), so the step kernels treat
+// every neighbour alike.
 //
 // A fluid cell's step runs in three phases: gather and moments; targets and
 // Newton (F, lam, m in shared memory); gather again, sensor, BGK and push.
@@ -622,77 +623,7 @@ __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
   if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// ---------------------------------------------------------------------------
-// Serving form: many resident lattices advanced by one packed launch per time
-// step.  A tile is one block of one lattice; each lattice keeps its own time
-// (and therefore its own AA parity) and stops at its own end time, so a packed
-// run gives every lattice exactly the arithmetic of stepping it alone.
-
-struct BatchEntry {
-  Desc d;
-  long long t0;     // the lattice's time at step index 0 of the current launch sequence
-  long long t_end;  // the lattice does not step past this time
-};
-
-struct Tile {
-  int lat;          // index into the batch entries
-  int pad;
-  long long cell0;  // first cell of the tile
-};
-
-template <class P, int BLK>
-__global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict__ E,
-                                                    const Tile* __restrict__ tiles, int s) {
-  extern __shared__ double smem[];
-  __shared__ unsigned int s_ctr[CTR_N];
-  __shared__ Desc sd;
-  __shared__ long long st;
-  const Tile tl = tiles[blockIdx.x];
-  if (threadIdx.x == 0) {
-    sd = E[tl.lat].d;
-    st = E[tl.lat].t0 + s < E[tl.lat].t_end ? E[tl.lat].t0 + s : -1;
-    sd.t = st;
-  }
-  for (int k = threadIdx.x; k < CTR_N; k += BLK) s_ctr[k] = 0;
-  load_exp_table();  // also publishes sd and st
-  const long long t = st;
-  if (t < 0) return;  // this lattice has reached its end time (uniform over the block)
-  const long long cell = tl.cell0 + threadIdx.x;
-  if (cell < sd.N && (sd.mask == nullptr || sd.mask[cell] == MASK_FLUID)) {
-    WS<BLK> w{smem + threadIdx.x};
-    // the lattice's constraint system (the z-mirror reduction serves FP64 lattices only)
-    if (sizeof(P) == 8 && sd.d2) {
-      if (t & 1) step_cell<true, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
-      else step_cell<false, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
-    } else {
-      if (t & 1) step_cell<true, P, BLK>(sd, cell, w, s_ctr);
-      else step_cell<false, P, BLK>(sd, cell, w, s_ctr);
-    }
-  }
-  flush_stats<BLK>(s_ctr, sd.ctr);
-}
-
-// Boundary fills of the lattices that have freestream or outflow cells.
-template <class P>
-__global__ void k_batch_fill(const BatchEntry* __restrict__ E, const Tile* __restrict__ tiles,
-                             int s) {
-  const Tile tl = tiles[blockIdx.x];
-  const BatchEntry& e = E[tl.lat];
-  const long long t = e.t0 + s;
-  if (t >= e.t_end) return;
-  const long long cell = tl.cell0 + threadIdx.x;
-  if (cell >= e.d.N) return;
-  if (t & 1) fill_odd_cell<P>(e.d, cell);
-  else fill_even_cell<P>(e.d, cell);
-}
-
-// After a launch sequence of n steps: every lattice's t0 moves on by n.
-__global__ void k_batch_advance(BatchEntry* E, int nlat, int n) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nlat) E[j].t0 += n;
-}
-
-// Library exponential and CUDA's exp side by side (diagnostic).
+// Library reciprocals and CUDA's IEEE divisions side by side (diagnostic).
 __global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y32, float* ref32,
                                long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -705,6 +636,7 @@ __global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y
   }
 }
 
+// Library exponential and CUDA's exp side by side (diagnostic).
 __global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
   load_exp_table();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;

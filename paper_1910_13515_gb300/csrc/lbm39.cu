@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/lbm39.h"
+#include "batch.cuh"
 #include "kernels.cuh"
 
 using namespace lbm39;

@@ -26,3 +26,20 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_traffic_key_ignores_comments_but_not_code():
+    """The key of bench.py's ncu traffic table hashes what the compiler acts on: a
+    comment or re-indentation keeps it, a changed token does not, and the serving
+    kernels (batch.cuh) are outside the step kernel's sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+    code = "int f(int a) {\n  return a * 2;  // twice\n}\n/* block\ncomment */ int g;\n"
+    same = "int f(int a) { return a * 2; }\n\n// another note\nint   g;"
+    changed = "int f(int a) {\n  return a * 3;  // twice\n}\nint g;\n"
+    assert bench.source_code_text(code) == bench.source_code_text(same)
+    assert bench.source_code_text(code) != bench.source_code_text(changed)
+    assert "batch.cuh" not in bench.KERNEL_SOURCES
+    for f in bench.KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_1910_13515_gb300", "csrc", f)), f
+    assert len(bench.kernel_source_hash()) == 16
