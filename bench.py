@@ -39,6 +39,9 @@ WORKLOADS = {
              "u_z then set to 0 (z-mirror symmetric), +-5% rho/T noise, seed 0, tau=0.55, "
              "alpha(eps) on",
     "sod": "Sod tube 400x1x1, outflow ends, tau=0.5 with alpha(eps)",
+    "poly": "polynomial-equilibrium comparison model (D3Q39 DDF-BGK, 4th-order Hermite "
+            "equilibrium), periodic 2048x2048x1, subsonic solenoidal flow rms Ma=0.3 at T=2/3, "
+            "+-1% rho/T noise, tau=0.6, plain BGK",
     "serve": "serving form: Poisson stream of 64 seeded requests (Riemann tubes 200-4000 cells, "
              "2-D shear layers 128^2-1024^2, 200-2000 steps), admitted into a 4 GiB budget",
 }
@@ -52,7 +55,7 @@ FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0),
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the step kernel's code they were
 # captured with; reported as null once that code differs (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": "1cf82e6ad8e4a458",
+NCU_TRAFFIC = {"kernel_hash": "d960ca4e67e7e364",
                "gb_per_launch": {"naca/fp64": 4.309, "naca/mixed": 3.177,
                                  "box128/fp64": 5.670, "box128/mixed": 3.207,
                                  "box2d/fp64": 4.583,
@@ -80,6 +83,10 @@ def kernel_source_hash() -> str:
             h.update(source_code_text(fh.read()).encode())
         h.update(b"\0")
     return h.hexdigest()[:16]
+# FP64 flops of one cell update of the polynomial comparison model, counted from its source
+# (2 per FMA, identical subexpressions once): moments 120, sum g 38, rho/u/T 21, cell
+# coefficients 35, shell coefficients 70, rest velocity 7, xi.u 32, 19 (xi, -xi) pairs x 20.
+POLY_FLOPS_PER_UPDATE = 703
 # populations read + written, and the per-cell solver state (lam and F: 52 FP64) read + written
 BYTES_PER_UPDATE = {"fp64": 78 * 8 * 2 + 52 * 8 * 2, "mixed": 78 * 4 * 2 + 52 * 8 * 2}
 
@@ -212,10 +219,57 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
+def poly_window(s, n: int = 128):
+    """n x n window of a quasi-2-D setup (periodic at the window edges): the polynomial
+    model's bounded CPU sample."""
+    import copy
+
+    import numpy as np
+    c = copy.copy(s)
+    sel = (np.arange(n)[:, None] * s.nx + np.arange(n)[None, :]).reshape(-1)
+    c.nx, c.ny, c.nz = n, n, 1
+    c.rho, c.u, c.T = s.rho[sel], np.ascontiguousarray(s.u[:, sel]), s.T[sel]
+    c.mask = s.mask[sel]
+    return c, f"{n}x{n}x1 window of the same lattice (periodic at the window edges)"
+
+
+def poly_oracle_steps(c, warmup: int, steps: int, budget_s: float = None):
+    """Time the polynomial model's oracle (numpy, as it stands) on setup c."""
+    from oracle import poly39
+    cfg = poly39.Config(nx=c.nx, ny=c.ny, nz=c.nz, gamma=c.gamma, tau=c.tau)
+    st = poly39.init(cfg, c.rho, c.u, c.T)
+    poly39.step(st, warmup)
+    done = 0
+    t0 = time.perf_counter()
+    while done < steps:
+        poly39.step(st, 1)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return c.ncells * done / dt / 1e6, done, dt
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle as it stands, on the host cores, each step a
     bounded sample (a window) of the same workload."""
     if rank != 0:
+        return
+    if args.workload == "poly":
+        from paper_1910_13515_gb300 import inputs
+        c, desc = poly_window(inputs.subsonic_box(2048, 2048, 1, seed=0))
+        v, done, dt = poly_oracle_steps(c, args.warmup, args.steps)
+        line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_text(args) + f" [oracle on a {desc}]",
+                           "cells": c.ncells},
+                "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1,
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     s = make_setup(args.workload, args.mach)
     c, desc = crop_setup(s, args.workload)
@@ -309,6 +363,124 @@ def run_serve(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_poly(args, rank, world, local):
+    """The polynomial-equilibrium comparison model on the paper's comparison size: value =
+    MLUPS of lbm39_poly_step (device-timed), roofline against the FP64 pipe (the binding one at
+    703 flops and 1248 bytes per update), e2e through PolyLattice with host buffers."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1910_13515_gb300 import inputs
+    from paper_1910_13515_gb300 import lbm39 as C
+    from paper_1910_13515_gb300.lattice import PolyLattice
+
+    dev = f"cuda:{local}"
+    s = inputs.subsonic_box(2048, 2048, 1, seed=0)
+    N = s.ncells
+    L = PolyLattice(s.nx, s.ny, s.nz, gamma=s.gamma, tau=s.tau, device=dev)
+    L.init(s.rho, s.u, s.T)
+    c0 = L.conserved()
+    L.step(args.warmup)
+    stream = L.stream
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for k in range(args.steps):
+            L.step(1)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    elapsed_s, units = reduce_over_ranks(evs[0].elapsed_time(evs[-1]) * 1e-3,
+                                         float(N * args.steps), dist, dev)
+    value = units / elapsed_s / 1e6
+    c1 = L.conserved()
+    step_ms = float(np.mean(per_step))
+    scratch = torch.empty(1 << 21, dtype=torch.float64, device=dev)
+    rc, peak_tf = C.lbm39_selftest_dfma(scratch.data_ptr(), scratch.numel() * 8,
+                                        stream.cuda_stream)
+    C.check(rc, "lbm39_selftest_dfma")
+    achieved_tf = POLY_FLOPS_PER_UPDATE * N / (step_ms * 1e-3) / 1e12
+    bytes_upd = 78 * 8 * 2
+    hbm_gbs = bytes_upd * N / (step_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4), "traffic": None,
+                "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
+                               "(of measured)",
+                "flops_per_cell_update": POLY_FLOPS_PER_UPDATE,
+                "flops_source": "counted from the kernel source, not from ncu",
+                "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": HBM_PEAK_GBS,
+                        "frac": round(hbm_gbs / HBM_PEAK_GBS, 4), "bytes_per_update": bytes_upd}}
+
+    # end to end through PolyLattice: fields uploaded from pinned host memory, then every step
+    # a step, a read-out and its copy into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory()
+        h_rho, h_u, h_T = pin(s.rho), pin(s.u), pin(s.T)
+        h_out = torch.empty((6, N), dtype=torch.float64).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.init(h_rho.to(dev, non_blocking=True), h_u.to(dev, non_blocking=True),
+               h_T.to(dev, non_blocking=True))
+        for _ in range(args.steps):
+            L.step(1)
+            r, u, T, p = L.read()
+            h_out[0].copy_(r, non_blocking=True)
+            h_out[1:4].copy_(u, non_blocking=True)
+            h_out[4].copy_(T, non_blocking=True)
+            h_out[5].copy_(p, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+        dt, units_e2e = reduce_over_ranks(time.perf_counter() - t0, float(N * args.steps),
+                                          dist, dev)
+        e2e = {"value": round(units_e2e / dt / 1e6, 3), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(5 * 8 * N / args.steps), "d2h_bytes_per_step": 6 * 8 * N,
+               "steps": args.steps, "includes": "upload of rho,u,T + lbm39_poly_init once, per "
+                                               "step lbm39_poly_step(1), lbm39_poly_read and the "
+                                               "copy of rho,u,T,p to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c, desc = poly_window(s)
+        v, done, dt = poly_oracle_steps(c, 0, 10 ** 6, budget_s=args.cpu_budget_s)
+        cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{desc}: {done} numpy oracle steps in {dt:.1f} s"}
+
+    if rank == 0:
+        drift = (np.abs(c1 - c0) / np.array([c0[0]] * 4 + [c0[4]])).tolist()
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(elapsed_s * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_text(args), "model": "polynomial", "cells": N,
+                       "conservation_drift_rel_mass_mom_xyz_energy":
+                           [float("%.3e" % v) for v in drift],
+                       "l2": "inputs larger than L2 (%.2f GB of populations)" % (
+                           bytes_upd / 2 * N / 1e9),
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "clocks": clocks, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": args.steps, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,6 +510,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, rank, world, local)
+        return
+    if args.workload == "poly":
+        run_poly(args, rank, world, local)
         return
 
     import numpy as np

@@ -163,8 +163,9 @@ int lbm39_step(lbm39_lattice* L, int64_t nsteps);
 /* Waits for the lattice's stream for at most timeout_us microseconds (< 0:
  * no limit).  *failed_cells (may be NULL) receives the Newton failures
  * since lbm39_init, summed over cells and steps (cell-steps that took the
- * five-invariant fallback equilibrium, see lbm39_step).  Returns LBM39_ERR_TIMEOUT if the work is still running,
- * LBM39_ERR_NEWTON if failed_cells > 0, else LBM39_OK. */
+ * five-invariant fallback equilibrium, see lbm39_step).  Returns
+ * LBM39_ERR_TIMEOUT if the work is still running, LBM39_ERR_NEWTON if
+ * failed_cells > 0, else LBM39_OK. */
 int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells);
 
 /* Enqueues the macroscopic fields of the current (pre-collision) state:

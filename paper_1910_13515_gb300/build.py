@@ -1,6 +1,7 @@
 """Build the CUDA library liblbm39.so (sm_103a) in-tree with nvcc.
 
-One translation unit (lbm39.cu with its headers), then linked into the shared library.
+Two translation units (lbm39.cu: the 13-moment model; poly.cu: the polynomial comparison
+model), compiled in parallel, then linked into one shared library.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler",
               "-fPIC", "-Xptxas", "-warn-spills"]
-SOURCES = ["lbm39.cu"]
+SOURCES = ["lbm39.cu", "poly.cu"]
 
 
 def nvcc() -> str:

@@ -624,8 +624,8 @@ __global__ void __launch_bounds__(BLK) k_conserved(Desc d, double* partials) {
 }
 
 // Library reciprocals and CUDA's IEEE divisions side by side (diagnostic).
-__global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y32, float* ref32,
-                               long long n) {
+static __global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y32,
+                                      float* ref32, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     y[i] = rcp64(x[i]);
@@ -637,7 +637,7 @@ __global__ void k_selftest_rcp(const double* x, double* y, double* ref, float* y
 }
 
 // Library exponential and CUDA's exp side by side (diagnostic).
-__global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
+static __global__ void k_selftest_exp(const double* x, double* y, double* ref, long long n) {
   load_exp_table();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -647,7 +647,7 @@ __global__ void k_selftest_exp(const double* x, double* y, double* ref, long lon
 }
 
 // FP64 FMA throughput probe: 8 independent chains per thread (diagnostic).
-__global__ void k_selftest_dfma(double* out, int iters, double a, double b) {
+static __global__ void k_selftest_dfma(double* out, int iters, double a, double b) {
   double x0 = threadIdx.x * 1e-9, x1 = x0 + 1e-9, x2 = x0 + 2e-9, x3 = x0 + 3e-9;
   double x4 = x0 + 4e-9, x5 = x0 + 5e-9, x6 = x0 + 6e-9, x7 = x0 + 7e-9;
   for (int i = 0; i < iters; ++i) {
@@ -660,7 +660,7 @@ __global__ void k_selftest_dfma(double* out, int iters, double a, double b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
-__global__ void k_sum_partials(const double* partials, int nblocks, double* out5) {
+static __global__ void k_sum_partials(const double* partials, int nblocks, double* out5) {
   const int k = threadIdx.x;
   if (k >= 5) return;
   double s = 0.0;

@@ -211,6 +211,18 @@ def box(n: int = 256, seed: int = 0, mach_rms: float = 0.8, T_mean: float = 0.5,
                  extra=dict(seed=seed, mach_rms=mach_rms, umax=umax))
 
 
+
+def subsonic_box(nx: int, ny: int, nz: int = 1, seed: int = 0, mach_rms: float = 0.3,
+                 T_mean: float = 2.0 / 3.0, noise: float = 0.01, gamma: float = 1.4,
+                 tau: float = 0.6) -> Setup:
+    """Generic subsonic periodic flow for the polynomial-equilibrium comparison model: the
+    box() recipe at rms |u| = mach_rms sqrt(gamma T_mean) about the lattice temperature 2/3,
+    rho and T with 1 % noise, plain BGK."""
+    s = box(seed=seed, shape=(nz, ny, nx), mach_rms=mach_rms, T_mean=T_mean, noise=noise,
+            gamma=gamma, tau=tau, kn_sensor=0)
+    s.name = f"subsonic_{nx}x{ny}x{nz}_s{seed}"
+    return s
+
 def uniform(nx: int, ny: int, nz: int, rho: float = 1.0, u=(0.3, -0.2, 0.1), T: float = 0.5,
             gamma: float = 1.4, tau: float = 0.6, kn_sensor: int = 1) -> Setup:
     """Uniform periodic flow (an invariant of the method)."""

@@ -155,3 +155,77 @@ class Lattice:
     @property
     def time(self) -> int:
         return int(self.stats().time)
+
+
+class PolyLattice:
+    """One periodic lattice of the polynomial-equilibrium comparison model (lbm39_poly.h):
+    D3Q39 DDF-BGK with the fourth-order Hermite equilibrium, FP64, over torch buffers."""
+
+    def __init__(self, nx: int, ny: int, nz: int, gamma: float = 1.4, tau: float = 0.6,
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None):
+        p = C.lbm39_default_params(nx, ny, nz)
+        p.kn_sensor = 0
+        p.gamma = gamma
+        p.tau = tau
+        self.params = p
+        self.device = torch.device(device)
+        self.N = nx * ny * nz
+        rc, pop_b, aux_b = C.lbm39_poly_query_bytes(p)
+        C.check(rc, "lbm39_poly_query_bytes")
+        self.pop = torch.empty((pop_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.aux = torch.empty((aux_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rc, h = C.lbm39_poly_create(p, self.pop.data_ptr(), self.aux.data_ptr(),
+                                    self.stream.cuda_stream)
+        C.check(rc, "lbm39_poly_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            C.lbm39_poly_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, n):
+        t = torch.as_tensor(np.ascontiguousarray(a, np.float64).reshape(-1), device=self.device) \
+            if not isinstance(a, torch.Tensor) else a.to(self.device, torch.float64).contiguous()
+        assert t.numel() == n
+        return t
+
+    def init(self, rho, u, T):
+        r, uu, t = self._dev(rho, self.N), self._dev(u, 3 * self.N), self._dev(T, self.N)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        C.check(C.lbm39_poly_init(self.h, r.data_ptr(), uu.data_ptr(), t.data_ptr()),
+                "lbm39_poly_init")
+        self.stream.synchronize()  # the kernel has read r, uu, t
+
+    def step(self, n: int = 1):
+        C.check(C.lbm39_poly_step(self.h, int(n)), "lbm39_poly_step")
+
+    def read(self):
+        """(rho, u (3,N), T, p) as float64 device tensors."""
+        out = torch.empty(6, self.N, dtype=torch.float64, device=self.device)
+        C.check(C.lbm39_poly_read(self.h, out[0].data_ptr(), out[1].data_ptr(),
+                                  out[4].data_ptr(), out[5].data_ptr()), "lbm39_poly_read")
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out[0], out[1:4], out[4], out[5]
+
+    def read_numpy(self):
+        r, u, T, p = self.read()
+        self.stream.synchronize()
+        return r.cpu().numpy(), u.cpu().numpy(), T.cpu().numpy(), p.cpu().numpy()
+
+    def conserved(self) -> np.ndarray:
+        """[mass, momentum x/y/z, total energy] (waits for the stream)."""
+        s = np.zeros(5)
+        C.check(C.lbm39_poly_conserved(self.h, s.ctypes.data), "lbm39_poly_conserved")
+        return s
+
+    @property
+    def time(self) -> int:
+        return int(C.lbm39_poly_time(self.h))

@@ -101,6 +101,15 @@ def _load():
         "lbm39_batch_destroy": (None, [vp]),
         "lbm39_destroy": (None, [vp]),
         "lbm39_strerror": (ctypes.c_char_p, [i]),
+        # lbm39_poly.h: the polynomial-equilibrium comparison model
+        "lbm39_poly_query_bytes": (i, [P, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+        "lbm39_poly_create": (i, [P, vp, vp, vp, ctypes.POINTER(vp)]),
+        "lbm39_poly_init": (i, [vp, vp, vp, vp]),
+        "lbm39_poly_step": (i, [vp, i64]),
+        "lbm39_poly_read": (i, [vp, vp, vp, vp, vp]),
+        "lbm39_poly_conserved": (i, [vp, vp]),
+        "lbm39_poly_time": (i64, [vp]),
+        "lbm39_poly_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,3 +254,43 @@ def lbm39_strerror(code: int) -> str:
 
 def exported_symbols() -> list:
     return [n for n in dir(_lib) if n.startswith("lbm39_")]
+
+
+# --- lbm39_poly.h ---------------------------------------------------------------------------
+
+def lbm39_poly_query_bytes(p: lbm39_params):
+    a = ctypes.c_size_t()
+    b = ctypes.c_size_t()
+    rc = _lib.lbm39_poly_query_bytes(ctypes.byref(p), ctypes.byref(a), ctypes.byref(b))
+    return rc, a.value, b.value
+
+
+def lbm39_poly_create(p: lbm39_params, pop_ptr, aux_ptr, stream_ptr):
+    """Returns (rc, handle)."""
+    h = ctypes.c_void_p()
+    rc = _lib.lbm39_poly_create(ctypes.byref(p), pop_ptr, aux_ptr, stream_ptr, ctypes.byref(h))
+    return rc, h.value
+
+
+def lbm39_poly_init(h, rho, u, T) -> int:
+    return _lib.lbm39_poly_init(h, rho, u, T)
+
+
+def lbm39_poly_step(h, nsteps: int) -> int:
+    return _lib.lbm39_poly_step(h, nsteps)
+
+
+def lbm39_poly_read(h, rho, u, T, p) -> int:
+    return _lib.lbm39_poly_read(h, rho, u, T, p)
+
+
+def lbm39_poly_conserved(h, sums5_host) -> int:
+    return _lib.lbm39_poly_conserved(h, sums5_host)
+
+
+def lbm39_poly_time(h) -> int:
+    return _lib.lbm39_poly_time(h)
+
+
+def lbm39_poly_destroy(h) -> None:
+    _lib.lbm39_poly_destroy(h)

@@ -1,5 +1,5 @@
 """Host-only checks of the C ABI: the library builds, loads and exports every symbol that
-include/lbm39.h declares; argument validation that happens before any CUDA call."""
+include/*.h declares; argument validation that happens before any CUDA call."""
 import ctypes
 import os
 import re
@@ -19,14 +19,19 @@ def C():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "lbm39.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm39_\w+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm39_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(C):
     names = declared_functions()
     assert "lbm39_step" in names and "lbm39_create" in names and len(names) >= 16
+    assert "lbm39_poly_step" in names and "lbm39_poly_create" in names
     lib = ctypes.CDLL(C.LIB_PATH)
     for n in names:
         assert hasattr(lib, n), n
@@ -95,3 +100,48 @@ def test_null_handles_and_strerror(C):
     for code in range(-7, 1):
         assert C.lbm39_strerror(code) != "unknown status"
     assert C.lbm39_strerror(-99) == "unknown status"
+
+
+def poly_params(C, nx=16, ny=8, nz=4):
+    p = C.lbm39_default_params(nx, ny, nz)
+    p.kn_sensor = 0
+    return p
+
+
+@pytest.mark.parametrize("field,value", [("kn_sensor", 1), ("precision", 1), ("tau", 0.49),
+                                         ("gamma", 1.0), ("nx", 0)])
+def test_poly_bad_params_rejected(C, field, value):
+    p = poly_params(C)
+    setattr(p, field, value)
+    assert C.lbm39_poly_query_bytes(p)[0] == C.LBM39_ERR_ARG
+
+
+def test_poly_sizes_and_state_checks_before_any_gpu_call(C):
+    p = poly_params(C, 10, 7, 3)
+    rc, pop, aux = C.lbm39_poly_query_bytes(p)
+    assert rc == C.LBM39_OK
+    assert pop == 8 * 78 * 256  # 210 cells, plane stride rounded up to 64
+    assert aux >= 8 * 5 * 1024
+    for a in range(3):  # every axis must be periodic
+        q = poly_params(C, 10, 7, 3)
+        q.periodic[a] = 0
+        assert C.lbm39_poly_query_bytes(q)[0] == C.LBM39_ERR_ARG
+    big = poly_params(C, 2048, 2048, 512)  # 2^31 cells
+    assert C.lbm39_poly_query_bytes(big)[0] == C.LBM39_ERR_ARG
+    fake = 1 << 20  # never dereferenced: create does no device work
+    assert C.lbm39_poly_create(p, fake + 8, fake, None)[0] == C.LBM39_ERR_ARG
+    rc, h = C.lbm39_poly_create(p, fake, fake, None)
+    assert rc == C.LBM39_OK and h
+    try:
+        assert C.lbm39_poly_time(h) == 0
+        assert C.lbm39_poly_step(h, 1) == C.LBM39_ERR_STATE
+        assert C.lbm39_poly_step(h, -1) == C.LBM39_ERR_ARG
+        assert C.lbm39_poly_read(h, None, None, None, None) == C.LBM39_ERR_STATE
+        s = np.zeros(5)
+        assert C.lbm39_poly_conserved(h, s.ctypes.data) == C.LBM39_ERR_STATE
+        assert C.lbm39_poly_init(h, None, None, None) == C.LBM39_ERR_ARG
+    finally:
+        C.lbm39_poly_destroy(h)
+    assert C.lbm39_poly_time(None) == -1
+    assert C.lbm39_poly_step(None, 1) == C.LBM39_ERR_ARG
+    C.lbm39_poly_destroy(None)
