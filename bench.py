@@ -40,7 +40,7 @@ WORKLOADS = {
              "alpha(eps) on",
     "sod": "Sod tube 400x1x1, outflow ends, tau=0.5 with alpha(eps)",
     "poly": "polynomial-equilibrium comparison model (D3Q39 DDF-BGK, 4th-order Hermite "
-            "equilibrium), periodic 2048x2048x1, subsonic solenoidal flow rms Ma=0.3 at T=2/3, "
+            "equilibrium), periodic NxNx1 (default 2048, the paper's comparison size), subsonic solenoidal flow rms Ma=0.3 at T=2/3, "
             "+-1% rho/T noise, tau=0.6, plain BGK",
     "serve": "serving form: Poisson stream of 64 seeded requests (Riemann tubes 200-4000 cells, "
              "2-D shear layers 128^2-1024^2, 200-2000 steps), admitted into a 4 GiB budget",
@@ -65,6 +65,13 @@ NCU_TRAFFIC = {"kernel_hash": "d960ca4e67e7e364",
 # in batch.cuh are not among them).
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                   "lbm39.cu")
+# The same for the polynomial comparison model's step kernel, and its ncu DRAM bytes per
+# launch (per lattice side n of the n x n x 1 workload; null once the code differs).
+POLY_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
+                "poly_eq.cuh", "poly.cu")
+POLY_NCU_TRAFFIC = {"kernel_hash": "16d713ebb5a1bc7d",
+                    # 2048: the 1024 capture scaled by the cell count (both exceed L2)
+                    "gb_per_launch": {"1024": 1.272, "2048": 5.087}}
 
 
 def source_code_text(text: str) -> str:
@@ -75,10 +82,10 @@ def source_code_text(text: str) -> str:
     return " ".join(text.split())
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_1910_13515_gb300", "csrc", f)) as fh:
             h.update(source_code_text(fh.read()).encode())
         h.update(b"\0")
@@ -125,6 +132,11 @@ def workload_text(args) -> str:
     text = WORKLOADS[args.workload]
     if args.workload.startswith("box") and args.mach != 0.8:
         text = text.replace("rms Ma=0.8", f"rms Ma={args.mach:g}")
+    if args.workload == "poly":
+        n = getattr(args, "poly_n", 2048)
+        text = text.replace("periodic NxNx1 (default 2048, the paper's comparison size)",
+                            f"periodic {n}x{n}x1" + (" (the paper's comparison size)"
+                                                      if n == 2048 else ""))
     return text
 
 
@@ -257,7 +269,8 @@ def run_reference(args, rank, world):
         return
     if args.workload == "poly":
         from paper_1910_13515_gb300 import inputs
-        c, desc = poly_window(inputs.subsonic_box(2048, 2048, 1, seed=0))
+        c, desc = poly_window(inputs.subsonic_box(args.poly_n, args.poly_n, 1, seed=0),
+                              min(128, args.poly_n))
         v, done, dt = poly_oracle_steps(c, args.warmup, args.steps)
         line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -384,7 +397,8 @@ def run_poly(args, rank, world, local):
     from paper_1910_13515_gb300.lattice import PolyLattice
 
     dev = f"cuda:{local}"
-    s = inputs.subsonic_box(2048, 2048, 1, seed=0)
+    n = args.poly_n
+    s = inputs.subsonic_box(n, n, 1, seed=0)
     N = s.ncells
     L = PolyLattice(s.nx, s.ny, s.nz, gamma=s.gamma, tau=s.tau, device=dev)
     L.init(s.rho, s.u, s.T)
@@ -415,8 +429,12 @@ def run_poly(args, rank, world, local):
     achieved_tf = POLY_FLOPS_PER_UPDATE * N / (step_ms * 1e-3) / 1e12
     bytes_upd = 78 * 8 * 2
     hbm_gbs = bytes_upd * N / (step_ms * 1e-3) / 1e9
+    traffic = None
+    if POLY_NCU_TRAFFIC["kernel_hash"] == kernel_source_hash(POLY_SOURCES):
+        traffic = POLY_NCU_TRAFFIC["gb_per_launch"].get(str(n))
     roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(peak_tf, 4),
-                "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
+                "traffic": round(traffic * 1e9) if traffic else None,
                 "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
                                "(of measured)",
                 "flops_per_cell_update": POLY_FLOPS_PER_UPDATE,
@@ -474,6 +492,7 @@ def run_poly(args, rank, world, local):
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
             "gpu_launches": args.steps, "cpu_baseline": cpu,
+            "kernel_hash": kernel_source_hash(POLY_SOURCES),
         }
         print(json.dumps(line), flush=True)
     L.close()
@@ -495,6 +514,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=0.8)
     ap.add_argument("--mach", type=float, default=0.8,
                     help="box workloads: rms Mach number of the initial velocity field")
+    ap.add_argument("--poly-n", type=int, default=2048,
+                    help="poly workload: lattice side n of the periodic n x n x 1 lattice")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision form: also run the FP64 path and report L1 error, drift, speedup")
     args = ap.parse_args()
