@@ -55,7 +55,7 @@ FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0),
 # DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
 # from ncu, per workload and precision, with the hash of the step kernel's code they were
 # captured with; reported as null once that code differs (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": "d960ca4e67e7e364",
+NCU_TRAFFIC = {"kernel_hash": "2573a64f33d8b3e6",
                "gb_per_launch": {"naca/fp64": 4.309, "naca/mixed": 3.177,
                                  "box128/fp64": 5.670, "box128/mixed": 3.207,
                                  "box2d/fp64": 4.583,

@@ -173,6 +173,16 @@ int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells);
  * may be NULL.  Non-fluid cells read 0. */
 int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p);
 
+/* Enqueues two per-cell fields of the current state into device arrays of N
+ * entries: eps (float64), the Knudsen sensor of Eq. DeltaAvg in FP64,
+ * (1/39) sum_i |f_i - f_i^eq| / f_i^eq, against the equilibrium the next step
+ * relaxes to; n_upd (int32), the Newton updates that step's solve takes from
+ * the stored multipliers (with its retry schedule), -1 where the solve fails
+ * and the cell takes the fallback.  These are the sensor and iteration maps of
+ * the airfoil run (Sec. 4).  Non-fluid cells read 0.  The state, the time and
+ * the counters do not change.  LBM39_ERR_STATE before lbm39_init. */
+int lbm39_diag_fields(lbm39_lattice* L, double* eps, int32_t* n_upd);
+
 /* As lbm39_read into host arrays; returns when they are written.  Page-locked
  * arrays (each one allocation) are written by the read-out kernel directly;
  * pageable ones through the staging area of the auxiliary buffer. */

@@ -17,6 +17,7 @@
 #include "../../include/lbm39.h"
 #include "batch.cuh"
 #include "kernels.cuh"
+#include "lattice_view.h"
 
 using namespace lbm39;
 
@@ -922,3 +923,18 @@ const char* lbm39_strerror(int status) {
 }
 
 }  // extern "C"
+
+namespace lbm39 {
+
+bool lattice_view(const lbm39_lattice* L, LatticeView* v) {
+  if (!L || !v) return false;
+  v->desc = L->desc;
+  v->desc.t = L->t;
+  v->stream = L->stream;
+  v->N = L->N;
+  v->mixed = L->mixed;
+  v->initialized = L->initialized;
+  return true;
+}
+
+}  // namespace lbm39

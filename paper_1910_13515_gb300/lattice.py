@@ -138,6 +138,16 @@ class Lattice:
                                   out[4].ctypes.data, out[5].ctypes.data), "lbm39_read_host")
         return out[0], out[1:4], out[4], out[5]
 
+    def diag_fields(self):
+        """(eps float64, n_upd int32) device tensors of the current state: the Knudsen sensor
+        and the Newton updates the next step takes (-1: the solve fails); state unchanged."""
+        eps = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        nupd = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        C.check(C.lbm39_diag_fields(self.h, eps.data_ptr(), nupd.data_ptr()),
+                "lbm39_diag_fields")
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return eps, nupd
+
     def stats(self) -> C.lbm39_stats_t:
         rc, s = C.lbm39_stats(self.h)
         C.check(rc, "lbm39_stats")

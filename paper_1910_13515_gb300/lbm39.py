@@ -93,6 +93,7 @@ def _load():
         "lbm39_selftest_rcp": (i, [vp, vp, vp, vp, vp, i64, vp]),
         "lbm39_selftest_dfma": (i, [ctypes.POINTER(ctypes.c_double), vp, sz, vp]),
         "lbm39_conserved_noalloc": (i, [vp, vp]),
+        "lbm39_diag_fields": (i, [vp, vp, vp]),
         "lbm39_batch_query_bytes": (i, [ctypes.c_int32, i64, ctypes.POINTER(sz)]),
         "lbm39_batch_create": (i, [ctypes.c_int32, i64, ctypes.c_int32, ctypes.c_int32, vp, vp,
                                    ctypes.POINTER(vp)]),
@@ -208,6 +209,10 @@ def lbm39_selftest_exp(x, y, ref, n: int, stream) -> int:
 
 def lbm39_selftest_rcp(x, y, ref, y32, ref32, n: int, stream) -> int:
     return _lib.lbm39_selftest_rcp(x, y, ref, y32, ref32, n, stream)
+
+
+def lbm39_diag_fields(h, eps, n_upd) -> int:
+    return _lib.lbm39_diag_fields(h, eps, n_upd)
 
 
 def lbm39_conserved_noalloc(h, sums5_host) -> int:
