@@ -43,3 +43,17 @@ def test_traffic_key_ignores_comments_but_not_code():
     for f in bench.KERNEL_SOURCES:
         assert os.path.exists(os.path.join(ROOT, "paper_1910_13515_gb300", "csrc", f)), f
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_poly_reference_arm_line():
+    """The comparison model's reference arm: its numpy oracle on a window of the same lattice."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "poly", "--poly-n", "64", "--steps", "1", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
+    assert d["config"]["cells"] == 64 * 64 and "64x64x1" in d["config"]["workload"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
