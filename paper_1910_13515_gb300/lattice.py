@@ -38,19 +38,62 @@ def params_from_setup(s: Setup, precision: int = C.LBM39_FP64, **over) -> C.lbm3
     return p
 
 
+class Guarded:
+    """A float64 buffer of n elements between two 64 KiB canary zones (a fixed bit pattern),
+    for debug runs: a kernel write before the start or past the end changes a canary.  The
+    buffer keeps the 256-byte alignment of the allocation."""
+
+    PAD = 8192                      # float64 elements per zone (64 KiB)
+    PATTERN = 0x7FF4C0DEC0DE5A5A    # a signalling-NaN bit pattern no kernel writes
+
+    def __init__(self, n: int, device):
+        self.full = torch.empty(n + 2 * self.PAD, dtype=torch.float64, device=device)
+        self.full[:self.PAD].view(torch.int64).fill_(self.PATTERN)
+        self.full[self.PAD + n:].view(torch.int64).fill_(self.PATTERN)
+        self.buf = self.full[self.PAD:self.PAD + n]
+
+    def intact(self) -> bool:
+        head = self.full[:self.PAD].view(torch.int64)
+        tail = self.full[self.PAD + self.buf.numel():].view(torch.int64)
+        return bool((head == self.PATTERN).all()) and bool((tail == self.PATTERN).all())
+
+
+def _buffers(pop_b: int, aux_b: int, device, debug: bool):
+    """(pop, aux) float64 device buffers of at least the given byte sizes, canary-guarded in
+    debug mode (then also the Guarded objects, else None)."""
+    n_pop, n_aux = (pop_b + 7) // 8, (aux_b + 7) // 8
+    if not debug:
+        return (torch.empty(n_pop, dtype=torch.float64, device=device),
+                torch.empty(n_aux, dtype=torch.float64, device=device), None)
+    g = (Guarded(n_pop, device), Guarded(n_aux, device))
+    return g[0].buf, g[1].buf, g
+
+
+def _check_guards(guards, where: str):
+    if guards is None:
+        return
+    if guards[0].full.is_cuda:
+        torch.cuda.synchronize(guards[0].full.device)
+    for name, g in zip(("population", "auxiliary"), guards):
+        if not g.intact():
+            raise RuntimeError(f"{where}: a kernel wrote outside the {name} buffer")
+
+
 class Lattice:
-    """Owns the device buffers of one lattice and its library handle."""
+    """Owns the device buffers of one lattice and its library handle.  debug=True puts
+    canary zones around the population and auxiliary buffers and checks them after every
+    init and step call (with a device synchronisation)."""
 
     def __init__(self, params: C.lbm39_params, mask: np.ndarray | None = None,
-                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None):
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None,
+                 debug: bool = False):
         self.params = params
         self.device = torch.device(device)
         self.N = params.nx * params.ny * params.nz
         rc, pop_b, aux_b = C.lbm39_query_bytes(params)
         C.check(rc, "lbm39_query_bytes")
         # 256-byte aligned by the caching allocator; float64 storage keeps 8-byte units
-        self.pop = torch.empty((pop_b + 7) // 8, dtype=torch.float64, device=self.device)
-        self.aux = torch.empty((aux_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.pop, self.aux, self._guards = _buffers(pop_b, aux_b, self.device, debug)
         self.mask = None
         # freestream, outflow or solid cells: the library runs a fill kernel after each pass
         self.has_fills = mask is not None and bool(
@@ -70,8 +113,8 @@ class Lattice:
 
     @classmethod
     def from_setup(cls, s: Setup, precision: int = C.LBM39_FP64, device="cuda", stream=None,
-                   **over) -> "Lattice":
-        L = cls(params_from_setup(s, precision, **over), s.mask, device, stream)
+                   debug: bool = False, **over) -> "Lattice":
+        L = cls(params_from_setup(s, precision, **over), s.mask, device, stream, debug)
         L.init(s.rho, s.u, s.T)
         return L
 
@@ -99,6 +142,7 @@ class Lattice:
         C.check(C.lbm39_init(self.h, r.data_ptr(), uu.data_ptr(), t.data_ptr()), "lbm39_init")
         self._keep = (r, uu, t)  # alive until the kernels have read them
         self.sync()
+        _check_guards(self._guards, "lbm39_init")
 
     def init_host(self, rho, u, T):
         """Initial condition from host arrays (copied through the library's staging)."""
@@ -110,6 +154,7 @@ class Lattice:
 
     def step(self, n: int = 1):
         C.check(C.lbm39_step(self.h, int(n)), "lbm39_step")
+        _check_guards(self._guards, "lbm39_step")
 
     def sync(self, timeout_us: int = -1) -> int:
         rc, failed = C.lbm39_sync(self.h, timeout_us)
@@ -172,18 +217,19 @@ class PolyLattice:
     D3Q39 DDF-BGK with the fourth-order Hermite equilibrium, FP64, over torch buffers."""
 
     def __init__(self, nx: int, ny: int, nz: int, gamma: float = 1.4, tau: float = 0.6,
-                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None):
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None,
+                 debug: bool = False):
         p = C.lbm39_default_params(nx, ny, nz)
         p.kn_sensor = 0
         p.gamma = gamma
         p.tau = tau
         self.params = p
+        self._debug = debug
         self.device = torch.device(device)
         self.N = nx * ny * nz
         rc, pop_b, aux_b = C.lbm39_poly_query_bytes(p)
         C.check(rc, "lbm39_poly_query_bytes")
-        self.pop = torch.empty((pop_b + 7) // 8, dtype=torch.float64, device=self.device)
-        self.aux = torch.empty((aux_b + 7) // 8, dtype=torch.float64, device=self.device)
+        self.pop, self.aux, self._guards = _buffers(pop_b, aux_b, self.device, self._debug)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         rc, h = C.lbm39_poly_create(p, self.pop.data_ptr(), self.aux.data_ptr(),
                                     self.stream.cuda_stream)
@@ -213,9 +259,11 @@ class PolyLattice:
         C.check(C.lbm39_poly_init(self.h, r.data_ptr(), uu.data_ptr(), t.data_ptr()),
                 "lbm39_poly_init")
         self.stream.synchronize()  # the kernel has read r, uu, t
+        _check_guards(self._guards, "lbm39_poly_init")
 
     def step(self, n: int = 1):
         C.check(C.lbm39_poly_step(self.h, int(n)), "lbm39_poly_step")
+        _check_guards(self._guards, "lbm39_poly_step")
 
     def read(self):
         """(rho, u (3,N), T, p) as float64 device tensors."""
