@@ -34,10 +34,10 @@
  * - Errors: every int-returning call returns LBM39_OK (0) or a negative
  *   lbm39_status; nothing is thrown across the ABI.  lbm39_strerror names
  *   the code.  Calls on one lattice are not thread-safe.
- * - Asynchrony: lbm39_step and lbm39_read enqueue work on the lattice's
- *   stream and return; lbm39_init, lbm39_sync, lbm39_stats and the *_host
- *   calls wait for it (lbm39_init reads back whether the initial state allows
- *   the z-mirror reduction of lbm39_params.reduce_2d).
+ * - Asynchrony: lbm39_step, lbm39_read and lbm39_diag_fields enqueue work on
+ *   the lattice's stream and return; lbm39_init, lbm39_sync, lbm39_stats and
+ *   the *_host calls wait for it (lbm39_init reads back whether the initial
+ *   state allows the z-mirror reduction of lbm39_params.reduce_2d).
  */
 #ifndef LBM39_H
 #define LBM39_H
