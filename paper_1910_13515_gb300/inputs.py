@@ -318,6 +318,7 @@ class Request:
     rid: int
     arrival_s: float
     setup: Setup
+    cancel_s: float | None = None   # the client withdraws the request at this time (None: never)
 
 
 def serving_requests(n: int = 64, seed: int = 0, rate_hz: float = 200.0,

@@ -6,7 +6,10 @@ are free, keeps admitted lattices resident, and advances all of them together
 through lbm39_batch_run (one packed launch per time step, runs of graph_steps
 steps replayed from a captured CUDA graph).  A lattice that reaches its step
 count is read out and freed, which frees memory for the next requests, so work
-that arrives while others run overlaps with them on the device.
+that arrives while others run overlaps with them on the device.  A request
+withdrawn by its client (Request.cancel_s) is dropped if it is still waiting, or
+released at the next run boundary (between steps) if it is resident; its memory
+goes to the next requests and the report lists it with the steps it completed.
 
 Scheduler holds the policy and is independent of the GPU (a test drives it with a
 fake backend); GpuBackend does the device work through the C ABI.
@@ -42,6 +45,7 @@ class Report:
     results: dict = field(default_factory=dict)
     max_resident: int = 0
     rounds: int = 0
+    cancelled: dict = field(default_factory=dict)   # rid -> steps completed before withdrawal
 
     @property
     def p50_ms(self) -> float:
@@ -77,6 +81,7 @@ class Scheduler:
         waiting: deque = deque()
         active: list = []
         done: dict = {}
+        cancelled: dict = {}
         used = 0
         t0 = self.clock()
         max_res = 0
@@ -86,6 +91,18 @@ class Scheduler:
             while pending and pending[0].arrival_s <= now:
                 r = pending.popleft()
                 waiting.append(Job(r, self.be.bytes_for(r.setup), r.setup.steps))
+            # withdrawals: waiting jobs are dropped, resident ones released between steps
+            gone = [j for j in waiting if _withdrawn(j, now)]
+            for j in gone:
+                waiting.remove(j)
+                cancelled[j.req.rid] = 0
+            gone = [j for j in active if _withdrawn(j, now)]
+            for j in gone:
+                self.be.release(j.handle)
+                used -= j.bytes
+                cancelled[j.req.rid] = j.done_steps
+                active.remove(j)
+                self.be.needs_set = True
             admitted = False
             while waiting and len(active) < self.max_resident and \
                     used + waiting[0].bytes <= self.budget:
@@ -117,11 +134,19 @@ class Scheduler:
                     done[j.req.rid] = j
                 active = [j for j in active if j.done_steps < j.steps]
                 self.be.needs_set = True
-        wall = max(j.t_done for j in done.values()) - min(j.req.arrival_s for j in done.values())
+        if done:
+            wall = max(j.t_done for j in done.values()) - min(j.req.arrival_s for j in done.values())
+        else:
+            wall = 0.0
         lat = [j.t_done - j.req.arrival_s for j in done.values()]
         cells = sum(j.req.setup.ncells * j.steps for j in done.values())
         return Report(lat, wall, cells, {rid: j.result for rid, j in done.items()}, max_res,
-                      rounds)
+                      rounds, cancelled)
+
+
+def _withdrawn(job: Job, now: float) -> bool:
+    c = getattr(job.req, "cancel_s", None)
+    return c is not None and c <= now
 
 
 class GpuBackend:

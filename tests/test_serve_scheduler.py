@@ -104,3 +104,40 @@ def test_oversized_request_is_rejected():
     except ValueError:
         return
     raise AssertionError("expected ValueError")
+
+
+def test_withdrawn_requests_are_dropped_or_released_between_steps():
+    """A waiting request withdrawn by its client is never admitted; a resident one is released
+    at the next run boundary and reported with the steps it completed; the memory it held goes
+    to the next request; the others still get exactly their steps."""
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    big = inputs.shear_layer(32, 1.0, steps=400)
+    reqs = [inputs.Request(0, 0.0, big, cancel_s=0.05),        # resident, withdrawn mid-run
+            inputs.Request(1, 0.0, big),                        # waits for 0's memory
+            inputs.Request(2, 0.001, big, cancel_s=0.002),      # withdrawn while waiting
+            inputs.Request(3, 0.0, inputs.shear_layer(8, 1.0, steps=30), cancel_s=10.0)]
+    budget = be.bytes_for(big) + be.bytes_for(reqs[3].setup)   # room for one big job at a time
+    rep = Scheduler(be, budget_bytes=budget, max_resident=4, chunk_steps=16, clock=clock,
+                    sleep=clock.sleep).run(reqs)
+    # request 0 runs alone (1 waits for memory, 3 queues behind 1) in rounds of 16 steps of
+    # 16 * 1024 us of fake time; its withdrawal at 0.05 s falls in the fourth round, so it is
+    # released at that round's end with 64 steps done
+    assert rep.cancelled[0] == 64
+    assert rep.cancelled[2] == 0
+    assert sorted(rep.results) == [1, 3]                       # 3 finished before its cancel time
+    assert rep.results[1] == 400 and rep.results[3] == 30
+    assert be.max_bytes_seen <= budget and not be.live        # everything released
+
+
+def test_no_withdrawal_changes_nothing():
+    reqs = make_requests()
+    runs = []
+    for cancel in (None, 1e9):
+        clock = FakeClock()
+        be = FakeBackend(clock)
+        rs = [inputs.Request(r.rid, r.arrival_s, r.setup, cancel_s=cancel) for r in reqs]
+        rep = Scheduler(be, budget_bytes=10 ** 6, max_resident=4, chunk_steps=8, clock=clock,
+                        sleep=clock.sleep).run(rs)
+        runs.append((rep.results, rep.latencies_s, rep.rounds, rep.cancelled))
+    assert runs[0] == runs[1] and runs[0][3] == {}
