@@ -1,5 +1,5 @@
 """The N > 1 path of bench.py (replicas, weak scaling) on CPU: two gloo ranks, max-over-ranks
-time and summed units, as the driver's torchrun launch would produce."""
+time and summed units, as a torchrun launch of bench.py would produce."""
 import os
 import socket
 import sys
