@@ -323,7 +323,7 @@ def reduce_over_ranks(elapsed_s: float, units: float, dist=None, device=None):
 
 
 def run_serve(args, rank, world, local):
-    """Config 5: the serving form.  value = aggregate MLUPS over the whole stream (all cells x
+    """The serving form.  value = aggregate MLUPS over the whole stream (all cells x
     steps of all requests / wall time from first arrival to last result); p50/p99 latency =
     arrival to result read.  Baseline: a sample of the same requests run one after another
     through plain lbm39_step (no packing)."""

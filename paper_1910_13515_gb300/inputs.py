@@ -62,7 +62,7 @@ def _flat(a3: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Config 1: Sod-type Riemann tube.
+# Sod-type Riemann tube.
 
 def riemann_tube(nx: int = 400, rho_l: float = 1.0, p_l: float = 1.0, rho_r: float = 0.125,
                  p_r: float = 0.1, gamma: float = 1.4, tau: float = 0.5, kn_sensor: int = 1,
@@ -96,7 +96,7 @@ def sod(nx: int = 400, **kw) -> Setup:
 
 
 # ---------------------------------------------------------------------------
-# Config 2: NACA0012 in supersonic flow (quasi-2-D, nz = 1).
+# NACA0012 in supersonic flow (quasi-2-D, nz = 1).
 
 def naca0012_half_thickness(xc: np.ndarray, t: float = 0.12) -> np.ndarray:
     """Analytic NACA 4-digit symmetric half-thickness (open trailing edge), in chords."""
@@ -142,7 +142,7 @@ def naca(nx: int = 2048, ny: int = 1024, chord: int = 400, mach: float = 1.5,
 
 
 # ---------------------------------------------------------------------------
-# Configs 3/4: periodic box with a random solenoidal velocity field.
+# Periodic box with a random solenoidal velocity field (FP64 and precision form).
 
 def limit_speed(u: np.ndarray, umax: float) -> np.ndarray:
     """Smoothly cap |u| below umax: u * umax tanh(|u|/umax) / |u| (direction kept)."""
@@ -237,7 +237,7 @@ def uniform(nx: int, ny: int, nz: int, rho: float = 1.0, u=(0.3, -0.2, 0.1), T: 
 
 
 # ---------------------------------------------------------------------------
-# Config 5 building blocks: shear layers and random Riemann tubes.
+# Serving-form building blocks: shear layers and random Riemann tubes.
 
 def shear_layer(L: int, mach: float, T_mean: float = 0.7, gamma: float = 1.4, tau: float = 0.55,
                 kn_sensor: int = 1, steps: int = 500, seed: int = 0) -> Setup:

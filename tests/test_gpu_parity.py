@@ -58,7 +58,7 @@ def test_parity_at_both_aa_parities(Lat, nsteps):
 
 
 def test_sod_tube_parity(Lat):
-    """Config 1 (400 x 1 x 1, outflow ends, tau = 1/2 with alpha(eps)) up to step 160, before
+    """The Sod tube (400 x 1 x 1, outflow ends, tau = 1/2 with alpha(eps)) up to step 160, before
     the waves reach the outflow cells.  Past that the undamped tau = 1/2 run amplifies
     round-off: a 1e-15 perturbation of the oracle's own initial state grows to ~3% in u by
     step 500 (test_sod_500_steps_is_roundoff_sensitive), so the full 500-step run is compared
@@ -276,9 +276,10 @@ def test_unrealisable_state_is_reported_not_faulted(Lat):
 
 @pytest.mark.parametrize("which", ["naca_full", "box_256"])
 def test_full_size_sampled_cells_match_oracle(Lat, which):
-    """At the full sizes of configs 2 and 3 (the launch configuration bench.py times): after a
-    few steps, sampled cells' next step is recomputed by the oracle from the GPU's own state
-    on a 7^d patch (the step's dependency cone) and must agree to 1e-11."""
+    """At the full sizes of the 2048 x 1024 NACA0012 airfoil and the 256^3 box (the launch
+    configuration bench.py times): after a few steps, sampled cells' next step is recomputed
+    by the oracle from the GPU's own state on a 7^d patch (the step's dependency cone) and
+    must agree to 1e-11."""
     if which == "naca_full":
         s = inputs.naca()  # 2048 x 1024, C = 400
         rng = np.random.default_rng(0)
