@@ -57,3 +57,23 @@ def test_poly_reference_arm_line():
     assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
     assert d["config"]["cells"] == 64 * 64 and "64x64x1" in d["config"]["workload"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_poly_helpers():
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import numpy as np
+
+    import bench
+    from paper_1910_13515_gb300 import inputs
+    s = inputs.subsonic_box(40, 30, 1, seed=1)
+    c, desc = bench.poly_window(s, 16)
+    assert (c.nx, c.ny, c.nz) == (16, 16, 1) and c.ncells == 256 and "16x16x1" in desc
+    # the window is the lattice's first 16 x 16 block, x fastest
+    np.testing.assert_array_equal(c.rho.reshape(16, 16), s.rho.reshape(30, 40)[:16, :16])
+    np.testing.assert_array_equal(c.u[1].reshape(16, 16), s.u[1].reshape(30, 40)[:16, :16])
+    for n, want in ((2048, "periodic 2048x2048x1 (the paper's comparison size)"),
+                    (1024, "periodic 1024x1024x1,")):
+        text = bench.workload_text(argparse.Namespace(workload="poly", poly_n=n, mach=0.8))
+        assert want in text, text
