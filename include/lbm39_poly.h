@@ -3,7 +3,7 @@
  * (sm_103a): BGK with a fourth-order polynomial equilibrium on the D3Q39
  * lattice, with a second population set for the extra degrees of freedom.
  *
- * Sec. 6 (performance comparison) of arXiv:1910.13515 times this model
+ * Sec. 5 (Implementation and efficiency) of arXiv:1910.13515 times this model
  * against the 13-moment model (lbm39.h) on a generic subsonic flow.  It names
  * the model without printing it; this library takes the following readings:
  * - f_i^eq is the Hermite expansion of the Maxwellian rho N(u, T I) about the

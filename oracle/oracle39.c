@@ -269,8 +269,8 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
 #define N5 5               /* constraints of the fallback equilibrium */
 #define FALLBACK_MAXIT 50  /* Newton updates of the fallback from its Gaussian start */
 #define FALLBACK_TOL 1e-12
-#define RETRY_MAXIT 3      /* full-solve updates of a cell that holds fallback multipliers */
-#define RETRY_PERIOD 8     /* such a cell retries the full solve once in this many steps */
+#define RETRY_MAXIT 3      /* full-solve updates of a cell on the fallback, on a retry step */
+#define RETRY_PERIOD 8     /* such a cell retries the full solve on steps t = 0 mod this */
 
 /* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
@@ -344,9 +344,7 @@ int o39_newton(const double *m, double *lam, double tol, int maxit, int min_upd,
  *   F_i = exp(mu_0 + mu . xi_i + mu_4 |xi_i|^2),  sum_i F_i phi5(xi_i) = [1, u, u^2 + D T],
  * which exists far beyond that cone and conserves mass, momentum and energy
  * (with g^eq = (2 C_v - D) T f^eq as for the full equilibrium).  It is solved
- * from the Gaussian start by the same damped Newton iteration; the cell's 13
- * multipliers keep their last accepted value, so the next step tries the full
- * solve again. */
+ * by the same damped Newton iteration as the full system. */
 
 static void basis5_i(int i, double *phi) {
   phi[0] = 1.0;
@@ -467,30 +465,30 @@ int o39_newton5(const double *m, double *mu, double tol, int maxit, int *n_upd_o
   return status;
 }
 
-/* After a fallback the cell keeps the five multipliers embedded in the 13:
- * lam = (mu_0, mu_x, mu_y, mu_z, mu_4, mu_4, mu_4, 0, 0, -0, 0, 0, 0), for
- * which exp(Phi lam) is the fallback equilibrium (|xi|^2 = xi_x^2 + xi_y^2 +
- * xi_z^2).  The negative zero of lam_9 marks the embedding (it changes no
- * exponent); a converged solve clears it (lam_9 + 0 turns -0 into +0 and
- * leaves every other value alone), so a solved state -- even one at rest,
- * which has the same shape -- is never taken for one.  A marked cell retries
- * the full solve from there with RETRY_MAXIT updates once every RETRY_PERIOD
- * steps (when time + cell index / 32 is a multiple of it: groups of 32
- * consecutive cells retry together, the groups in turn) and otherwise with
- * none, i.e. it goes to the fallback, which starts from the stored mu.  A cell back inside the cone converges and resumes; one still
- * outside costs a fallback solve from a close start instead of a full budget. */
-static int is_fallback_embedding(const double *lam) {
-  if (!(lam[9] == 0.0 && signbit(lam[9]))) return 0;
-  for (int k = 7; k < NM; ++k)
-    if (k != 9 && (lam[k] != 0.0 || signbit(lam[k]))) return 0;
-  return memcmp(&lam[4], &lam[5], sizeof(double)) == 0 &&
-         memcmp(&lam[5], &lam[6], sizeof(double)) == 0;
-}
+/* Failure policy (reading; the paper is silent).  A cell whose full solve
+ * fails takes the fallback equilibrium and keeps its five multipliers
+ * embedded in the 13,
+ *   lam = (mu_0, mu_x, mu_y, mu_z, mu_4, mu_4, mu_4, 0, 0, 0, 0, 0, 0),
+ * for which exp(Phi lam) is the fallback equilibrium (|xi|^2 = xi_x^2 +
+ * xi_y^2 + xi_z^2), and a per-cell flag "on the fallback" is set.  On the
+ * next steps a flagged cell does not repeat the full solve from scratch:
+ *  - on every step t that is a multiple of RETRY_PERIOD it tries the full
+ *    solve again from the embedding, with at most RETRY_MAXIT updates; a cell
+ *    that has come back inside the cone converges and its flag is cleared;
+ *  - on the other steps it takes no update (only the residual of the
+ *    embedding is checked), and the fallback starts from the stored mu.
+ * Cells outside the cone usually stay outside for many steps (the region is
+ * carried by the flow), so this bounds the work of a cell that cannot
+ * converge to a fallback solve from a close start, while a cell that has
+ * re-entered the cone returns to the 13-moment equilibrium within
+ * RETRY_PERIOD steps.  The rule depends on the time step alone.  If the
+ * fallback fails as well, the cell keeps the multipliers the full solve left,
+ * its equilibrium is evaluated there, and its flag is cleared. */
 
-/* The fallback for the state (u, T), from the stored mu (warm, a fallback
- * embedding) or the Gaussian start (warm NULL).  On success lam becomes the
- * embedding of its multipliers and F = exp(Phi lam); otherwise lam and F are
- * left as they are.  Returns the fallback's status. */
+/* The fallback for the state (u, T), from the stored mu (warm, the first five
+ * entries of an embedding) or the Gaussian start (warm NULL).  On success lam
+ * becomes the embedding of its multipliers and F = exp(Phi lam); otherwise
+ * lam and F are left as they are.  Returns the fallback's status. */
 static int fallback_into(const double *u, double T, const double *warm, double *lam, double *F) {
   double m5[N5], mu[N5], F5[Q];
   o39_targets5(u, T, m5);
@@ -503,7 +501,6 @@ static int fallback_into(const double *u, double T, const double *warm, double *
   for (int k = 0; k < NM; ++k) lam[k] = 0.0;
   for (int k = 0; k < 4; ++k) lam[k] = mu[k];
   lam[4] = lam[5] = lam[6] = mu[4];
-  lam[9] = -0.0;
   o39_feq_norm(lam, F);
   return 0;
 }
@@ -550,11 +547,12 @@ void o39_cell_macros(const o39_params *p, const double *f, const double *g,
 /* One BGK collision of one fluid cell (Sec. 3 and Eq. DeltaAvg / alpha):
  * macros -> MB targets -> Newton (warm start lam) -> f^eq, g^eq = (2C_v-D) T f^eq
  * -> eps, alpha -> h* = h - (h - h^eq)/(tau alpha) for h = f and h = g.
- * phase: time step + cell index / 32 (it schedules the retries of fallback cells).
+ * t: the time step being taken; on_fb: the cell's "on the fallback" flag (in
+ * and out), which with t decides the solve's budget (failure policy above).
  * reading: eps uses f only and the same alpha relaxes f and g (Pr = 1).
- * In place on f, g, lam.  Returns the Newton status. */
-int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, int64_t phase,
-                     int *n_upd, double *eps_out, double *alpha_out) {
+ * In place on f, g, lam, on_fb.  Returns the Newton status. */
+int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, uint8_t *on_fb,
+                     int64_t t, int *n_upd, double *eps_out, double *alpha_out) {
   build_lattice();
   double cv = 1.0 / (p->gamma - 1.0);
   double rho, u[3], T;
@@ -563,15 +561,19 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, int
   o39_targets(u, T, m);
   double lam_in[NM];
   memcpy(lam_in, lam, sizeof lam_in);
-  const int marked = is_fallback_embedding(lam);
-  /* a marked cell off its retry step gets no update: it stays on the fallback
-   * unless its embedding already meets the 13 constraints */
-  const int maxit = !marked ? p->newton_maxit : (phase % RETRY_PERIOD == 0 ? RETRY_MAXIT : 0);
+  const int flagged = *on_fb != 0;
+  int maxit = p->newton_maxit;
+  if (flagged) maxit = (t % RETRY_PERIOD == 0) ? RETRY_MAXIT : 0;
   int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
-  if (st) {  /* counted as a failure: the cell is on the fallback this step */
-    if (fallback_into(u, T, marked ? lam_in : NULL, lam, F)) o39_feq_norm(lam, F);
+  if (st) {  /* counted as a failure: the cell takes the fallback this step */
+    if (fallback_into(u, T, flagged ? lam_in : NULL, lam, F) == 0) {
+      *on_fb = 1;
+    } else {
+      o39_feq_norm(lam, F);
+      *on_fb = 0;
+    }
   } else {
-    lam[9] += 0.0;  /* a solved state carries no embedding mark */
+    *on_fb = 0;
   }
   double feq[Q], geq[Q];
   for (int i = 0; i < Q; ++i) {
@@ -593,9 +595,10 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, int
 }
 
 /* Equilibrium populations and multipliers of a state (rho, u, T) from the
- * Gaussian cold start (used for initial conditions and far-field cells). */
+ * Gaussian cold start (used for initial conditions and far-field cells).
+ * on_fb (may be NULL): set to 1 where the fallback equilibrium was taken. */
 int o39_equilibrium(const o39_params *p, double rho, const double *u, double T,
-                    double *feq, double *geq, double *lam, int maxit) {
+                    double *feq, double *geq, double *lam, int maxit, uint8_t *on_fb) {
   build_lattice();
   double cv = 1.0 / (p->gamma - 1.0);
   double m[NM], F[Q];
@@ -603,7 +606,9 @@ int o39_equilibrium(const o39_params *p, double rho, const double *u, double T,
   o39_gaussian_guess(u, T, lam);
   int nu = 0;
   int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, &nu, F);
-  if (st) fallback_into(u, T, NULL, lam, F);
+  int fb = 0;
+  if (st) fb = fallback_into(u, T, NULL, lam, F) == 0;
+  if (on_fb) *on_fb = (uint8_t)fb;
   for (int i = 0; i < Q; ++i) {
     feq[i] = rho * F[i];
     geq[i] = (2.0 * cv - DIM) * T * feq[i];
@@ -625,22 +630,25 @@ static int wrap(int a, int n) {
 
 /* Initial condition: every fluid cell at its local equilibrium f^eq(rho,u,T),
  * g^eq, with lam from a cold-start Newton; other cells hold zeros.
- * u is given as three planes u[d*N + cell].  Returns the failed-cell count. */
+ * u is given as three planes u[d*N + cell].  on_fb: per-cell "on the
+ * fallback" flags (out).  Returns the failed-cell count. */
 int64_t o39_init(const o39_params *p, const uint8_t *mask, const double *rho,
                  const double *u, const double *T, double *f, double *g,
-                 double *lam, int maxit) {
+                 double *lam, uint8_t *on_fb, int maxit) {
   build_lattice();
   int64_t N = (int64_t)p->nx * p->ny * p->nz;
   int64_t failed = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : failed)
   for (int64_t c = 0; c < N; ++c) {
+    on_fb[c] = 0;
     if (mask[c] != M_FLUID) {
       for (int i = 0; i < Q; ++i) { f[c * Q + i] = 0.0; g[c * Q + i] = 0.0; }
       for (int k = 0; k < NM; ++k) lam[c * NM + k] = 0.0;
       continue;
     }
     double uc[3] = {u[c], u[N + c], u[2 * N + c]};
-    failed += o39_equilibrium(p, rho[c], uc, T[c], f + c * Q, g + c * Q, lam + c * NM, maxit);
+    failed += o39_equilibrium(p, rho[c], uc, T[c], f + c * Q, g + c * Q, lam + c * NM, maxit,
+                              on_fb + c);
   }
   return failed;
 }
@@ -697,16 +705,17 @@ void o39_stream(const o39_params *p, const uint8_t *mask, const double *fpost,
       }
 }
 
-/* nsteps full time steps: collide every fluid cell, then stream (pull) from
- * the post-collision array back into f, g.  Returns failed Newton solves. */
+/* nsteps full time steps from time t0: collide every fluid cell, then stream
+ * (pull) from the post-collision array back into f, g.  on_fb: per-cell
+ * "on the fallback" flags (in and out).  Returns failed Newton solves. */
 int64_t o39_step(const o39_params *p, const uint8_t *mask, double *f, double *g,
-                 double *lam, int64_t t0, int nsteps, o39_stats *st) {
+                 double *lam, uint8_t *on_fb, int64_t t0, int nsteps, o39_stats *st) {
   build_lattice();
   int64_t N = (int64_t)p->nx * p->ny * p->nz;
   double *fp = (double *)malloc(sizeof(double) * N * Q);
   double *gp = (double *)malloc(sizeof(double) * N * Q);
   double feq_inf[Q], geq_inf[Q], lam_inf[NM];
-  o39_equilibrium(p, p->rho_inf, p->u_inf, p->T_inf, feq_inf, geq_inf, lam_inf, 200);
+  o39_equilibrium(p, p->rho_inf, p->u_inf, p->T_inf, feq_inf, geq_inf, lam_inf, 200, NULL);
   int64_t failed_total = 0;
   for (int t = 0; t < nsteps; ++t) {
     int64_t failed = 0, upd = 0, fluid = 0;
@@ -717,8 +726,8 @@ int64_t o39_step(const o39_params *p, const uint8_t *mask, double *f, double *g,
       if (mask[c] != M_FLUID) continue;
       int nu = 0;
       double eps, alpha;
-      failed += o39_collide_cell(p, fp + c * Q, gp + c * Q, lam + c * NM, t0 + t + (c >> 5), &nu,
-                                 &eps, &alpha);
+      failed += o39_collide_cell(p, fp + c * Q, gp + c * Q, lam + c * NM, on_fb + c, t0 + t,
+                                 &nu, &eps, &alpha);
       upd += nu;
       fluid += 1;
       int b = nu < 31 ? nu : 31;

@@ -95,14 +95,14 @@ def lib():
         _lib.o39_targets5.restype = None
         _lib.o39_gaussian_guess5.argtypes = [vp, d, vp]
         _lib.o39_gaussian_guess5.restype = None
-        _lib.o39_collide_cell.argtypes = [P, vp, vp, vp, i64, vp, vp, vp]
+        _lib.o39_collide_cell.argtypes = [P, vp, vp, vp, vp, i64, vp, vp, vp]
         _lib.o39_collide_cell.restype = ctypes.c_int
-        _lib.o39_equilibrium.argtypes = [P, d, vp, d, vp, vp, vp, ctypes.c_int]
+        _lib.o39_equilibrium.argtypes = [P, d, vp, d, vp, vp, vp, ctypes.c_int, vp]
         _lib.o39_equilibrium.restype = ctypes.c_int
-        _lib.o39_init.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        _lib.o39_init.argtypes = [P, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         _lib.o39_init.restype = i64
         _lib.o39_stream.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
-        _lib.o39_step.argtypes = [P, vp, vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
+        _lib.o39_step.argtypes = [P, vp, vp, vp, vp, vp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
         _lib.o39_step.restype = i64
         _lib.o39_macros.argtypes = [P, vp, vp, vp, vp, vp, vp, vp]
         _lib.o39_conserved.argtypes = [P, vp, vp, vp, vp]
@@ -258,20 +258,21 @@ def cell_macros(cfg: Config, f, g):
     return rho.value, u, T.value
 
 
-def collide_cell(cfg: Config, f, g, lam, phase: int = 0):
-    """One collision in place on copies; returns (f*, g*, lam, n_upd, eps, alpha, status).
-    phase (time step + cell index / 32) schedules the retries of a cell on the fallback."""
+def collide_cell(cfg: Config, f, g, lam, on_fallback: bool = False, t: int = 0):
+    """One collision in place on copies; returns (f*, g*, lam, n_upd, eps, alpha, status,
+    on_fallback).  on_fallback (the cell's flag) and t (the time step being taken) decide the
+    solve's budget under the failure policy (oracle39.c)."""
     f = _f64(f).copy()
     g = _f64(g).copy()
     lam = _f64(lam).copy()
+    fb = ctypes.c_uint8(1 if on_fallback else 0)
     nu = ctypes.c_int()
     eps = ctypes.c_double()
     al = ctypes.c_double()
     p = cfg.params()
-    st = lib().o39_collide_cell(ctypes.byref(p), _p(f), _p(g), _p(lam), int(phase),
-                                ctypes.byref(nu),
-                                ctypes.byref(eps), ctypes.byref(al))
-    return f, g, lam, nu.value, eps.value, al.value, st
+    st = lib().o39_collide_cell(ctypes.byref(p), _p(f), _p(g), _p(lam), ctypes.byref(fb), int(t),
+                                ctypes.byref(nu), ctypes.byref(eps), ctypes.byref(al))
+    return f, g, lam, nu.value, eps.value, al.value, st, bool(fb.value)
 
 
 def equilibrium(cfg: Config, rho, u, T, maxit=200):
@@ -281,7 +282,7 @@ def equilibrium(cfg: Config, rho, u, T, maxit=200):
     lam = np.zeros(NM)
     p = cfg.params()
     st = lib().o39_equilibrium(ctypes.byref(p), float(rho), _p(_f64(u)), float(T), _p(feq),
-                               _p(geq), _p(lam), int(maxit))
+                               _p(geq), _p(lam), int(maxit), None)
     return feq, geq, lam, st
 
 
@@ -290,6 +291,8 @@ def equilibrium(cfg: Config, rho, u, T, maxit=200):
 
 @dataclass
 class State:
+    """Oracle lattice state: populations f, g (N, 39), multipliers lam (N, 13), the per-cell
+    "on the fallback" flags on_fb (N,) of the failure policy, and the time t."""
     cfg: Config
     mask: np.ndarray
     f: np.ndarray
@@ -297,6 +300,11 @@ class State:
     lam: np.ndarray
     t: int = 0
     stats: Stats = field(default_factory=Stats)
+    on_fb: np.ndarray = None
+
+    def __post_init__(self):
+        if self.on_fb is None:
+            self.on_fb = np.zeros(self.lam.shape[0], np.uint8)
 
 
 def init(cfg: Config, mask, rho, u, T, allow_failed: bool = False) -> State:
@@ -311,20 +319,22 @@ def init(cfg: Config, mask, rho, u, T, allow_failed: bool = False) -> State:
     f = np.zeros((N, Q))
     g = np.zeros((N, Q))
     lam = np.zeros((N, NM))
+    on_fb = np.zeros(N, np.uint8)
     p = cfg.params()
     failed = lib().o39_init(ctypes.byref(p), _p(mask), _p(rho), _p(u), _p(T), _p(f), _p(g),
-                            _p(lam), int(cfg.init_maxit))
+                            _p(lam), _p(on_fb), int(cfg.init_maxit))
     if failed and not allow_failed:
         raise RuntimeError(f"oracle init: {failed} cells failed the Newton solve")
-    st = State(cfg, mask, f, g, lam)
+    st = State(cfg, mask, f, g, lam, on_fb=on_fb)
     st.init_failed = int(failed)
     return st
 
 
 def step(st: State, nsteps: int) -> int:
     p = st.cfg.params()
+    st.on_fb = np.ascontiguousarray(st.on_fb, dtype=np.uint8)
     failed = lib().o39_step(ctypes.byref(p), _p(st.mask), _p(st.f), _p(st.g), _p(st.lam),
-                            int(st.t), int(nsteps), ctypes.byref(st.stats))
+                            _p(st.on_fb), int(st.t), int(nsteps), ctypes.byref(st.stats))
     st.t += nsteps
     return int(failed)
 

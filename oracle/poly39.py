@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle of the paper's comparison model: BGK with a fourth-order
 polynomial equilibrium on the D3Q39 lattice, with a second population set g that
-carries the energy of the extra degrees of freedom, so that gamma is free (Sec. 6,
-performance comparison; the double-population approach of Sec. 3).
+carries the energy of the extra degrees of freedom, so that gamma is free (Sec. 5,
+Implementation and efficiency; the double-population approach of Sec. 3).
 
 TEST INFRASTRUCTURE ONLY: the test suite and the CPU-baseline leg of ``bench.py``
 are the only callers.  The CUDA library never imports this module and this module

@@ -365,16 +365,18 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
 constexpr int N5 = 5;
 constexpr int FALLBACK_MAXIT = 50;
 constexpr double FALLBACK_TOL = 1e-12;
-// After a fallback the cell keeps its five multipliers embedded in the 13:
-// lam = (mu_0, mu_x, mu_y, mu_z, mu_4, mu_4, mu_4, 0, 0, -0, 0, 0, 0), whose
-// exp(Phi lam) is the fallback equilibrium.  The negative zero of lam_9 marks
-// the embedding (it changes no exponent); a converged solve clears it (lam_9 + 0
-// turns -0 into +0 and leaves any other value alone), so a solved state, even
-// one at rest with the same shape, is never taken for one.  A marked cell
-// retries the full solve from there with RETRY_MAXIT updates once every
-// RETRY_PERIOD steps (when time + cell index / 32 is a multiple of it: the 32
-// cells of a warp retry together, the warps in turn) and otherwise goes
-// straight to the fallback, which starts from the stored mu.
+// Failure policy (reading; the paper is silent).  After a fallback the cell
+// keeps its five multipliers embedded in the 13: lam = (mu_0, mu_x, mu_y, mu_z,
+// mu_4, mu_4, mu_4, 0, 0, 0, 0, 0, 0), whose exp(Phi lam) is the fallback
+// equilibrium, and it is flagged "on the fallback".  The flag is stored in
+// the multipliers themselves: lam_9 = -0 in the embedding (it changes no
+// exponent).  A converged solve, or a fallback that fails too, clears it
+// (lam_9 + 0 turns -0 into +0 and leaves any other value alone), so a solved
+// state, even one at rest with the same shape, is never taken for one.  A
+// flagged cell retries the full solve from the embedding with RETRY_MAXIT
+// updates on the time steps that are multiples of RETRY_PERIOD, and on the
+// other steps takes no update and goes straight to the fallback, which starts
+// from the stored mu.  The schedule depends on the time step alone.
 constexpr int RETRY_MAXIT = 3;
 constexpr int RETRY_PERIOD = 8;  // a power of two
 

@@ -64,8 +64,7 @@ __global__ void __launch_bounds__(BLK) k_diag_fields(Desc d, int odd, double* ep
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
   const bool marked = is_fallback_embedding<BLK>(lam);
-  const int maxit =
-      !marked ? d.ph.maxit : (((d.t + (cell >> 5)) & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0);
+  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
   const NewtonResult nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   double f[Q];

@@ -305,7 +305,8 @@ __device__ __forceinline__ void eval_at_lam(WS<BLK> w) {
 }
 
 // Where the 13-moment solve failed or took no update: the fallback's
-// multipliers embedded in lam (lam unchanged if that fails too), and F =
+// multipliers embedded in lam and marked (lam unchanged but unmarked if the
+// fallback fails too), and F =
 // exp(Phi lam) evaluated as the full solve does, so the cached F stays exact
 // (for an embedding it is the fallback equilibrium up to rounding).  retry:
 // the cell came in with a fallback embedding, whose five multipliers (still in
@@ -319,16 +320,25 @@ __device__ __noinline__ void fallback_cell(const double* state, long long Np, lo
 #pragma unroll
     for (int k = 0; k < N5; ++k) warm[k] = state[k * Np + cell];
   }
+  WS<BLK> lam = w.at(WS_LAM);
   if (fallback_equilibrium<BLK>(w, T, retry ? warm : nullptr) == 0) {
-    WS<BLK> lam = w.at(WS_LAM), mu = w.at(WS_M);
+    WS<BLK> mu = w.at(WS_M);
 #pragma unroll
     for (int k = 0; k < 4; ++k) lam[k] = mu[k];
     lam[4] = lam[5] = lam[6] = mu[4];
 #pragma unroll
     for (int k = 7; k < NM; ++k) lam[k] = 0.0;
-    lam[9] = -0.0;  // the embedding mark
+    lam[9] = -0.0;  // the embedding mark: on the fallback
+  } else {
+    lam[9] = lam[9] + 0.0;  // the fallback failed too: not on the fallback
   }
   eval_at_lam<BLK>(w);  // F = exp(Phi lam), the cached value the next solve starts from
+}
+
+// Newton budget of a cell on the fallback at time step t: RETRY_MAXIT on the
+// steps that are multiples of RETRY_PERIOD, else none.
+__device__ __forceinline__ int retry_budget(long long t) {
+  return (t & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0;
 }
 
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
@@ -345,10 +355,9 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
   const bool marked = is_fallback_embedding<BLK>(lam);
-  // a marked cell off its retry step gets no update (it stays on the fallback
+  // a marked cell off a retry step gets no update (it stays on the fallback
   // unless its embedding already meets the 13 constraints)
-  const int maxit =
-      !marked ? d.ph.maxit : (((d.t + (cell >> 5)) & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0);
+  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
   const NewtonResult nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark

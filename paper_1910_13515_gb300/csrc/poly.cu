@@ -1,4 +1,4 @@
-// poly.cu -- the paper's comparison model (Sec. 6) on the GPU: D3Q39
+// poly.cu -- the paper's comparison model (Sec. 5) on the GPU: D3Q39
 // double-distribution BGK with the fourth-order polynomial equilibrium of
 // poly_eq.cuh, for periodic lattices, on the in-place AA pattern and the
 // generated moment sums of the 13-moment step (kernels.cuh); and its C ABI

@@ -1,4 +1,4 @@
-// poly_eq.cuh -- equilibrium of the paper's comparison model (Sec. 6): the
+// poly_eq.cuh -- equilibrium of the paper's comparison model (Sec. 5): the
 // fourth-order polynomial (Hermite) equilibrium on D3Q39, host and device.
 //
 // f_i^eq = rho w_i sum_{n<=4} a^(n) : H^(n)(xi_i) / (n! th^n), with th = 2/3

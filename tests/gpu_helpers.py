@@ -39,6 +39,19 @@ def lib_to_oracle_perm():
     return np.array([idx[tuple(v)] for v in ov])
 
 
+def fallback_flags(lam):
+    """The oracle's per-cell "on the fallback" flags of multipliers (n, 13) read from the
+    library's state: the library marks a cell on the fallback by lambda_9 = -0 inside the
+    embedding of the five fallback multipliers (lambda_4 = lambda_5 = lambda_6, the other
+    second- and third-order multipliers +0)."""
+    lam = np.asarray(lam)
+    rest = np.delete(lam[:, 7:], 2, axis=1)
+    bits = rest.view(np.uint64)
+    return ((lam[:, 9] == 0) & np.signbit(lam[:, 9]) & (bits == 0).all(axis=1)
+            & (lam[:, 4].view(np.uint64) == lam[:, 5].view(np.uint64))
+            & (lam[:, 5].view(np.uint64) == lam[:, 6].view(np.uint64))).astype(np.uint8)
+
+
 def patch_from_checkpoint(L, buf, cx, cy, cz, r=3):
     """Populations (oracle order) and multipliers of the (2r+1)^d patch around (cx,cy,cz) from a
     checkpoint taken at even time (pre-collision populations in their own slots)."""

@@ -29,13 +29,13 @@ def Lat():
 
 def oracle_fields(s, st):
     """(eps, n_upd) of the oracle state st: one collision per fluid cell on copies, with the
-    retry phase of the step (time + cell index / 32); -1 where the solve fails."""
+    cell's fallback flag and the state's time step; -1 where the solve fails."""
     cfg = oracle_cfg(s)
     eps = np.zeros(s.ncells)
     nupd = np.zeros(s.ncells, np.int64)
     for c in np.flatnonzero(s.mask == 0):
-        _, _, _, nu, e, _, status = o.collide_cell(cfg, st.f[c], st.g[c], st.lam[c],
-                                                   phase=st.t + (int(c) >> 5))
+        _, _, _, nu, e, _, status, _ = o.collide_cell(cfg, st.f[c], st.g[c], st.lam[c],
+                                                      on_fallback=bool(st.on_fb[c]), t=st.t)
         eps[c] = e
         nupd[c] = -1 if status else nu
     return eps, nupd

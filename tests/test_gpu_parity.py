@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import TOL, oracle_cfg, patch_from_checkpoint, rel_diffs, run_oracle
+from gpu_helpers import (TOL, fallback_flags, oracle_cfg, patch_from_checkpoint, rel_diffs,
+                         run_oracle)
 from oracle import oracle39 as o
 from paper_1910_13515_gb300 import inputs
 
@@ -253,7 +254,7 @@ def test_cells_outside_the_cone_take_the_fallback(Lat):
     assert L.sync() >= b.sum() * 21
     c1 = np.array(L.stats().conserved)
     assert np.all(np.abs(c1 - c0) <= 1e-12 * np.array([c0[0]] * 4 + [c0[4]])), c1 - c0
-    for n in (1, 3):
+    for n in (1, 3, 9, 17):  # across the retry steps 0, 8 and 16 of the failure policy
         L2 = Lat.from_setup(s)
         L2.step(n)
         L2.sync()
@@ -261,6 +262,27 @@ def test_cells_outside_the_cone_take_the_fallback(Lat):
         o.step(st, n)
         d = rel_diffs(L2.read_numpy(), o.macros(st), s.mask, s.gamma)
         assert max(d) <= TOL, (n, d)
+
+
+def test_naca_with_developing_fallback_cells_parity(Lat):
+    """A small NACA0012 lattice at Ma 2.0 (u_inf = 1.67 at T_inf = 0.5): from step ~10 the flow
+    reaches states outside the 13-moment cone, and by step 40 several hundred cells are on the
+    fallback, retrying the full solve on steps 8, 16, 24 and 32.  The GPU matches the oracle to
+    1e-11, with the same failure count and the same cells flagged on the fallback."""
+    s = inputs.naca(nx=96, ny=48, chord=24, x_le=24, mach=2.0)
+    n = 40
+    L, g, fg = gpu_run(Lat, s, n)
+    st, fo = run_oracle(s, n)
+    assert fo > 1000 and fg == fo
+    d = rel_diffs(g, o.macros(st), s.mask, s.gamma)
+    assert max(d) <= TOL, d
+    buf = L.checkpoint()
+    Np = (s.ncells + 63) // 64 * 64
+    lam = buf[256:].view(torch.float64)[78 * Np: 91 * Np].view(13, Np)[:, :s.ncells]
+    flags = fallback_flags(lam.T.contiguous().cpu().numpy())
+    fl = s.mask == 0
+    assert st.on_fb[fl].sum() > 100
+    assert np.array_equal(flags[fl], st.on_fb[fl])
 
 
 def test_unrealisable_state_is_reported_not_faulted(Lat):
@@ -309,7 +331,8 @@ def test_full_size_sampled_cells_match_oracle(Lat, which):
         cfg = o.Config(nx=px, ny=py, nz=pz, periodic=(1, 1, 1), gamma=cfg0.gamma, tau=cfg0.tau,
                        kn_sensor=cfg0.kn_sensor, rho_inf=cfg0.rho_inf, u_inf=cfg0.u_inf,
                        T_inf=cfg0.T_inf)
-        st = o.State(cfg, np.ascontiguousarray(s.mask[cells]), f, g, lam)
+        st = o.State(cfg, np.ascontiguousarray(s.mask[cells]), f, g, lam, t=4,
+                     on_fb=fallback_flags(lam))
         assert o.step(st, 1) == 0
         ro, uo, To, po = o.macros(st)
         k = len(cells) // 2

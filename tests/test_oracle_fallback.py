@@ -73,8 +73,8 @@ def test_collision_outside_the_cone_conserves(oracle):
         f = rho * F * (1 + 1e-3 * RNG.uniform(-1, 1, 39))
         g = (2 * cv - 3) * T * rho * F
         lam = oracle.gaussian_guess(u, T)
-        fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f, g, lam)
-        assert st == 1
+        fs, gs, lam2, nu, eps, al, st, fb = oracle.collide_cell(cfg, f, g, lam)
+        assert st == 1 and fb
         c2 = (vel.astype(float) ** 2).sum(1)
         m0 = np.r_[_invariants(vel, f)[:4], f @ c2 + g.sum()]
         m1 = np.r_[_invariants(vel, fs)[:4], fs @ c2 + gs.sum()]
@@ -83,8 +83,9 @@ def test_collision_outside_the_cone_conserves(oracle):
 
 def test_failed_cell_keeps_embedded_fallback_multipliers_and_retries_cheaply(oracle):
     """After a fallback the 13 multipliers are the five embedded (lambda_4..6 equal, the rest of
-    the second and third orders zero), so exp(Phi lambda) is the fallback equilibrium; the next
-    collision of a cell still outside the cone spends at most 3 full-solve updates."""
+    the second and third orders zero), so exp(Phi lambda) is the fallback equilibrium, and the cell
+    is flagged; the next collision of a cell still outside the cone spends at most 3 full-solve
+    updates (none off a retry step)."""
     vel, _, _ = oracle.lattice()
     cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
     cv = 1.0 / (cfg.gamma - 1.0)
@@ -93,38 +94,35 @@ def test_failed_cell_keeps_embedded_fallback_multipliers_and_retries_cheaply(ora
     F5 = oracle.newton5(u, T)[1]
     f, g = rho * F5, (2 * cv - 3) * T * rho * F5
     lam = oracle.gaussian_guess(u, T)
-    lam[7] = 1e-3  # not of the embedded form: a full budget
-    fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f, g, lam)
-    assert st == 1 and nu > 3
+    lam[7] = 1e-3  # an unflagged cell: the full budget
+    fs, gs, lam2, nu, eps, al, st, fb = oracle.collide_cell(cfg, f, g, lam)
+    assert st == 1 and fb and nu > 3
     assert np.all(lam2[7:] == 0) and lam2[4] == lam2[5] == lam2[6]
-    assert np.signbit(lam2[9]) and not np.signbit(lam2[7])  # the embedding mark
     F = oracle.feq_norm(lam2)
     want = np.r_[1.0, u, u @ u + 3 * T]
     assert np.all(np.abs(_invariants(vel, F) - want) <= 1e-12 * np.maximum(1, np.abs(want)))
-    fs2, gs2, lam3, nu2, eps2, al2, st2 = oracle.collide_cell(cfg, f, g, lam2)
-    assert st2 == 1 and nu2 <= 3
-    assert np.all(lam3[7:] == 0) and np.allclose(oracle.feq_norm(lam3), F, rtol=1e-12, atol=0)
+    for t, most in ((0, 3), (5, 0)):
+        _, _, lam3, nu2, _, _, st2, fb2 = oracle.collide_cell(cfg, f, g, lam2, on_fallback=True,
+                                                              t=t)
+        assert st2 == 1 and fb2 and nu2 <= most
+        assert np.all(lam3[7:] == 0) and np.allclose(oracle.feq_norm(lam3), F, rtol=1e-12, atol=0)
 
 
 def test_a_solved_rest_state_is_not_taken_for_a_fallback(oracle):
-    """A cell at rest has multipliers of the embedded shape; it must keep the full Newton budget
-    when a strong change arrives (the mark, not the shape, identifies a fallback)."""
+    """A cell at rest has multipliers of the embedded shape; unflagged, it keeps the full Newton
+    budget when a strong change arrives (the flag, not the shape, identifies a fallback)."""
     cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
-    cv = 1.0 / (cfg.gamma - 1.0)
     feq, geq, lam, st = oracle.equilibrium(cfg, 1.0, np.zeros(3), 0.5)
     assert st == 0
-    lam[7:] = 0.0           # the exact shape that symmetric arithmetic gives at rest,
-    lam[5] = lam[6] = lam[4]  # without the mark
+    lam[7:] = 0.0           # the exact shape that symmetric arithmetic gives at rest
+    lam[5] = lam[6] = lam[4]
     # a cell at rest receives populations of a fast, hot state (a shock arriving)
     f2, g2, _, _ = oracle.equilibrium(cfg, 2.5, np.array([0.9, 0.0, 0.0]), 0.8)
-    fs, gs, lam2, nu, eps, al, st = oracle.collide_cell(cfg, f2, g2, lam)
-    assert st == 0 and nu > 3
+    fs, gs, lam2, nu, eps, al, st, fb = oracle.collide_cell(cfg, f2, g2, lam, t=3)
+    assert st == 0 and not fb and nu > 3
 
 
-def test_marked_cell_retries_only_on_its_phase(oracle):
-    """A cell on the fallback tries the full solve (3 updates) only when time + cell index / 32
-    is a multiple of 8; on other steps it takes the fallback directly (no update, still
-    counted)."""
+def _flagged_outside_cell(oracle):
     cfg = oracle.Config(nx=1, tau=0.6, kn_sensor=1)
     cv = 1.0 / (cfg.gamma - 1.0)
     (u, T), rho = OUTSIDE[0], 0.954
@@ -132,9 +130,41 @@ def test_marked_cell_retries_only_on_its_phase(oracle):
     F5 = oracle.newton5(u, T)[1]
     f, g = rho * F5, (2 * cv - 3) * T * rho * F5
     lam = oracle.gaussian_guess(u, T)
-    lam[7] = 1e-3
-    lam2 = oracle.collide_cell(cfg, f, g, lam)[2]
-    assert np.signbit(lam2[9])
-    for phase, most in ((1, 0), (7, 0), (8, 3), (16, 3)):
-        _, _, lam3, nu, _, _, st = oracle.collide_cell(cfg, f, g, lam2, phase=phase)
-        assert st == 1 and nu <= most and np.signbit(lam3[9])
+    lam2, fb = oracle.collide_cell(cfg, f, g, lam)[2::5]
+    assert fb
+    return cfg, f, g, lam2
+
+
+def test_flagged_cell_retries_on_multiples_of_eight(oracle):
+    """The failure policy's schedule: a flagged cell tries the full solve (3 updates, its
+    residual is above the tolerance so all 3 are taken or the line search gives up) exactly on
+    the time steps that are multiples of 8, and takes no update on every other step."""
+    cfg, f, g, lam2 = _flagged_outside_cell(oracle)
+    for t in range(0, 33):
+        nu, st, fb = (lambda r: (r[3], r[6], r[7]))(
+            oracle.collide_cell(cfg, f, g, lam2, on_fallback=True, t=t))
+        assert st == 1 and fb
+        if t % 8 == 0:
+            assert 1 <= nu <= 3, (t, nu)
+        else:
+            assert nu == 0, (t, nu)
+
+
+def test_retry_schedule_is_the_same_for_every_cell(oracle):
+    """On a lattice every flagged cell follows the same schedule, wherever it sits: a periodic
+    row of identical cells outside the cone keeps identical populations and multipliers after
+    each step (no cell-index dependence), and its Newton updates per step are 0 off the retry
+    steps."""
+    cfg1, f, g, lam2 = _flagged_outside_cell(oracle)
+    n = 70
+    cfg = oracle.Config(nx=n, ny=1, nz=1, tau=0.6, kn_sensor=1)
+    st = oracle.State(cfg, np.zeros(n, np.uint8), np.tile(f, (n, 1)), np.tile(g, (n, 1)),
+                      np.tile(lam2, (n, 1)), on_fb=np.ones(n, np.uint8))
+    prev = 0
+    for t in range(10):
+        oracle.step(st, 1)
+        assert (st.f == st.f[0]).all() and (st.lam == st.lam[0]).all()
+        upd = st.stats.newton_updates - prev
+        prev = st.stats.newton_updates
+        assert (upd == 0) == (t % 8 != 0), (t, upd)
+        assert st.on_fb.all()

@@ -1,5 +1,5 @@
 """Pins of the oracle's fourth-order polynomial-equilibrium DDF-BGK model (the paper's
-comparison model, Sec. 6) against mathematics independent of the oracle: Maxwell-Boltzmann
+comparison model, Sec. 5) against mathematics independent of the oracle: Maxwell-Boltzmann
 moments by Gauss-Hermite quadrature, the Hermite projection integral, the weights' rest
 state, conservation, and the sound speed and viscosity the model must produce."""
 import itertools

@@ -58,15 +58,16 @@ def _worker(rank, world, port, out):
     st = o.State(ext, _layers(full.mask.reshape(-1, 1), z0 - H, z1 + H, nz, plane).ravel(),
                  _layers(full.f, z0 - H, z1 + H, nz, plane),
                  _layers(full.g, z0 - H, z1 + H, nz, plane),
-                 _layers(full.lam, z0 - H, z1 + H, nz, plane))
+                 _layers(full.lam, z0 - H, z1 + H, nz, plane),
+                 on_fb=_layers(full.on_fb, z0 - H, z1 + H, nz, plane))
     lo, hi = (rank - 1) % world, (rank + 1) % world
     n_halo = H * plane
     for _ in range(STEPS):
         # pre-collision state of the interior layers next to each face -> the neighbours
         send_lo = [torch.from_numpy(np.ascontiguousarray(a[n_halo:2 * n_halo]))
-                   for a in (st.f, st.g, st.lam)]
+                   for a in (st.f, st.g, st.lam, st.on_fb)]
         send_hi = [torch.from_numpy(np.ascontiguousarray(a[-2 * n_halo:-n_halo]))
-                   for a in (st.f, st.g, st.lam)]
+                   for a in (st.f, st.g, st.lam, st.on_fb)]
         recv_lo = [torch.empty_like(t) for t in send_lo]
         recv_hi = [torch.empty_like(t) for t in send_hi]
         reqs = []
@@ -80,9 +81,9 @@ def _worker(rank, world, port, out):
             reqs.append(dist.irecv(t, lo, tag=2))
         for r in reqs:
             r.wait()
-        for a, t in zip((st.f, st.g, st.lam), recv_lo):
+        for a, t in zip((st.f, st.g, st.lam, st.on_fb), recv_lo):
             a[:n_halo] = t.numpy()
-        for a, t in zip((st.f, st.g, st.lam), recv_hi):
+        for a, t in zip((st.f, st.g, st.lam, st.on_fb), recv_hi):
             a[-n_halo:] = t.numpy()
         assert o.step(st, 1) == 0
     out[rank] = (st.f[n_halo:-n_halo].copy(), st.g[n_halo:-n_halo].copy(),
