@@ -2,12 +2,18 @@
 """Benchmark of the D3Q39 13-moment DDF lattice Boltzmann step (MLUPS) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload naca|box256|box384|sod] [--precision fp64|mixed]
+                    [--workload box256|box384|box128|box2d|naca|sod|poly|serve]
+                    [--precision fp64|mixed] [--sections precision,serving,airfoil|none]
 
 A step is one full time step (collide + stream with the mask rules) over the whole
-lattice.  Inputs are synthetic and seeded (paper_1910_13515_gb300.inputs).  For N > 1
-(torchrun, one process per GPU) every rank runs its own replica of the workload
-(weak scaling; the step has no exchange between replicas).  Rank 0 prints one JSON line.
+lattice.  Inputs are synthetic and seeded (paper_1910_13515_gb300.inputs).  The default
+line is the 3-D periodic 256^3 box in FP64 (rms Ma 0.8); the same line carries the other
+parts of the metric: the precision form on the 256^3 and 384^3 boxes against the FP64
+path, a serving run (Poisson request stream, p50/p99 time-to-solution, aggregate MLUPS
+against serial stepping) and the 2048x1024 NACA0012 airfoil (early window and developed
+flow).  For N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
+workload (weak scaling; the step has no exchange between replicas) and the extra sections
+are skipped.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -322,24 +328,23 @@ def reduce_over_ranks(elapsed_s: float, units: float, dist=None, device=None):
     return float(t.item()), float(u.item())
 
 
-def run_serve(args, rank, world, local):
-    """The serving form.  value = aggregate MLUPS over the whole stream (all cells x
-    steps of all requests / wall time from first arrival to last result); p50/p99 latency =
-    arrival to result read.  Baseline: a sample of the same requests run one after another
-    through plain lbm39_step (no packing)."""
-    import numpy as np
+def serving_section(args, local, n_requests: int, rate_hz: float, seed: int = 0):
+    """The serving form on a Poisson stream of n_requests seeded requests: aggregate MLUPS
+    over the whole stream (all cells x steps of all requests / wall time from first arrival
+    to last result) and p50/p99 time-to-solution (arrival to result read).  Baseline: a
+    sample of the same requests run one after another through plain lbm39_step (no
+    packing), each with its own init and read-out, as a served request has."""
     import torch
 
     from paper_1910_13515_gb300 import inputs
     from paper_1910_13515_gb300.lattice import Lattice
     from paper_1910_13515_gb300.serve import GpuBackend, Scheduler
 
-    torch.cuda.set_device(local)
     prec = 0 if args.precision == "fp64" else 1
-    reqs = inputs.serving_requests(64, seed=rank, rate_hz=args.serve_rate)
+    reqs = inputs.serving_requests(n_requests, seed=seed, rate_hz=rate_hz)
     be = GpuBackend(precision=prec, max_lattices=64, max_cells=1 << 25,
                     graph_steps=8, device=f"cuda:{local}")
-    warm = inputs.serving_requests(4, seed=1000 + rank, rate_hz=1e6, shear_sizes=(128,),
+    warm = inputs.serving_requests(4, seed=1000 + seed, rate_hz=1e6, shear_sizes=(128,),
                                    riemann_range=(200, 400), steps_range=(16, 24))
     Scheduler(be, 4 << 30, 64, chunk_steps=64).run(warm)
     with ClockSampler(local) as clk:
@@ -357,22 +362,34 @@ def run_serve(args, rank, world, local):
         cs += r.setup.ncells * r.setup.steps
         L.close()
     serial = cs / (time.perf_counter() - t0) / 1e6
+    return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "budget_gib": 4,
+            "cell_steps": rep.cell_steps, "max_resident": rep.max_resident,
+            "rounds": rep.rounds,
+            "p50_ms": round(rep.p50_ms, 2), "p99_ms": round(rep.p99_ms, 2),
+            "aggregate_mlups": round(rep.mlups, 3), "serial_mlups": round(serial, 3),
+            "speedup_vs_serial": round(rep.mlups / serial, 3),
+            "serial_sample": f"{len(sample)} of the requests, one at a time",
+            "wall_s": round(rep.wall_s, 2), "clocks": clocks}
+
+
+def run_serve(args, rank, world, local):
+    """The serving form as its own line: value = aggregate MLUPS of the request stream."""
+    import torch
+    torch.cuda.set_device(local)
+    sec = serving_section(args, local, 64, args.serve_rate, seed=rank)
     if rank == 0:
-        line = {"metric": METRIC, "value": round(rep.mlups, 3), "unit": "MLUPS",
-                "n_gpus": world, "steps": sum(r.setup.steps for r in reqs), "warmup": 4,
+        prec = 0 if args.precision == "fp64" else 1
+        line = {"metric": METRIC, "value": sec["aggregate_mlups"], "unit": "MLUPS",
+                "n_gpus": world, "steps": sec["cell_steps"], "warmup": 4,
                 "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32-storage/f64-solve",
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS["serve"], "requests": len(reqs),
-                           "cell_steps": rep.cell_steps, "budget_gib": 4,
-                           "max_resident": rep.max_resident, "rounds": rep.rounds,
+                "config": {"workload": WORKLOADS["serve"], "requests": sec["requests"],
+                           "cell_steps": sec["cell_steps"], "budget_gib": 4,
+                           "max_resident": sec["max_resident"], "rounds": sec["rounds"],
                            "arrival_rate_hz": args.serve_rate},
-                "serving": {"p50_ms": round(rep.p50_ms, 2), "p99_ms": round(rep.p99_ms, 2),
-                            "aggregate_mlups": round(rep.mlups, 3),
-                            "serial_mlups": round(serial, 3),
-                            "speedup_vs_serial": round(rep.mlups / serial, 3),
-                            "serial_sample": f"{len(sample)} of the requests, one at a time"},
-                "clocks": clocks, "gpu_launches": None}
+                "serving": {k: v for k, v in sec.items() if k != "clocks"},
+                "clocks": sec["clocks"], "gpu_launches": None}
         print(json.dumps(line), flush=True)
 
 
@@ -500,13 +517,148 @@ def run_poly(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def timed_steps(L, steps: int, local: int, barrier=lambda: None):
+    """K steps of lattice L, each bracketed by CUDA events on the lattice's stream, with the
+    clocks sampled meanwhile: (per-step ms list, total ms, clock summary)."""
+    import torch
+    stream = L.stream
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for k in range(steps):
+            L.step(1)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return per_step, evs[0].elapsed_time(evs[-1]), clocks
+
+
+def counter_shares(st0, st1, cell_steps: int) -> dict:
+    """Newton-update and alpha-branch shares of the cell updates between two stats reads."""
+    hist = [st1.newton_hist[k] - st0.newton_hist[k] for k in range(32)]
+    return {"newton_updates_per_cell": round((st1.newton_updates - st0.newton_updates)
+                                             / cell_steps, 4),
+            "newton_updates_share_0_1_2_3_4plus":
+                [round(h / cell_steps, 4) for h in hist[:4]] + [round(sum(hist[4:]) / cell_steps, 4)],
+            "alpha_branch_share": [round((st1.eps_hist[k] - st0.eps_hist[k]) / cell_steps, 4)
+                                   for k in range(4)],
+            "fallback_share": round((st1.failed_cells - st0.failed_cells) / cell_steps, 6)}
+
+
+def l1_rel(a, b, fl):
+    """L1 differences of (rho, u, T) fields a against b over the fluid cells, each relative to
+    the L1 norm of b (u: of |u|)."""
+    import numpy as np
+    (ra, ua, Ta), (rb, ub, Tb) = a[:3], b[:3]
+    return [float(np.abs(ra[fl] - rb[fl]).mean() / np.abs(rb[fl]).mean()),
+            float(np.abs(ua[:, fl] - ub[:, fl]).mean() / np.sqrt((ub[:, fl] ** 2).sum(0)).mean()),
+            float(np.abs(Ta[fl] - Tb[fl]).mean() / np.abs(Tb[fl]).mean())]
+
+
+def drift_rel(c0, c1):
+    """Relative change of the conserved sums (mass, momentum x/y/z relative to the mass,
+    energy)."""
+    import numpy as np
+    c0, c1 = np.array(c0), np.array(c1)
+    return (np.abs(c1 - c0) / np.array([abs(c0[0])] * 4 + [abs(c0[4])])).tolist()
+
+
+def precision_form_section(args, local, s256, fp64_256):
+    """The precision form (FP32 deviation storage, FP32 collision, FP64 moments and solve) on
+    the 256^3 and 384^3 boxes, against the FP64 path on the same input after the same steps
+    (the FP64 path is parity-checked against the FP64 oracle): MLUPS, speed-up, L1 error in
+    rho/u/T, conservation drift.  fp64_256: (fields, MLUPS) of the FP64 256^3 run."""
+    import torch
+
+    from paper_1910_13515_gb300 import lbm39 as C
+    from paper_1910_13515_gb300.lattice import Lattice
+    dev = f"cuda:{local}"
+    out = {}
+    nsteps = args.warmup + args.steps
+    for n in (256, 384):
+        s = s256 if n == 256 else make_setup("box384", args.mach)
+        fl = s.mask == 0
+        if n == 256:
+            ref, ref_mlups = fp64_256
+        else:
+            Lf = Lattice.from_setup(s, precision=C.LBM39_FP64, device=dev)
+            Lf.step(args.warmup)
+            _, ms, _ = timed_steps(Lf, args.steps, local)
+            ref_mlups = s.ncells * args.steps / (ms * 1e-3) / 1e6
+            ref = Lf.read_numpy()
+            Lf.close()
+            del Lf
+            torch.cuda.empty_cache()
+        Lm = Lattice.from_setup(s, precision=C.LBM39_MIXED, device=dev)
+        c0 = Lm.stats().conserved
+        Lm.step(args.warmup)
+        st0 = Lm.stats()
+        per_step, ms, clocks = timed_steps(Lm, args.steps, local)
+        st1 = Lm.stats()
+        mlups = s.ncells * args.steps / (ms * 1e-3) / 1e6
+        state = Lm.read_numpy()
+        Lm.close()
+        del Lm
+        torch.cuda.empty_cache()
+        drift = drift_rel(c0, st1.conserved)
+        sec = {"cells": s.ncells, "mlups": round(mlups, 3), "fp64_mlups": round(ref_mlups, 3),
+               "speedup_vs_fp64": round(mlups / ref_mlups, 3),
+               "compared_after_steps": nsteps,
+               "l1_rel_vs_fp64_rho_u_T": [float("%.3e" % v) for v in l1_rel(state, ref, fl)],
+               "conservation_drift_rel_mass_mom_xyz_energy": [float("%.3e" % v) for v in drift],
+               "conservation_drift_per_1000_steps": [float("%.3e" % (v * 1000 / nsteps))
+                                                     for v in drift],
+               "sm_mhz": clocks.get("sm_mhz")}
+        sec.update(counter_shares(st0, st1, int(fl.sum()) * args.steps))
+        out[f"box{n}"] = sec
+    out["note"] = ("FP32 populations stored as deviations from the rest equilibrium at "
+                   "(rho, T) = (1, 0.5); the FP64 path it is compared with is parity-checked "
+                   "against the FP64 oracle; mass and momentum drift relative to the total mass")
+    return out
+
+
+def airfoil_section(args, local, developed_at: int):
+    """The 2048x1024 NACA0012 airfoil (Ma 1.5, Re 1e4, C = 400), FP64: the rate over the early
+    window of the impulsive start (steps W..W+K) and over K steps of the developed flow from
+    step `developed_at` on (bow and trailing shocks formed, cells outside the 13-moment cone
+    on the fallback)."""
+    from paper_1910_13515_gb300 import lbm39 as C
+    from paper_1910_13515_gb300.lattice import Lattice
+    s = make_setup("naca")
+    L = Lattice.from_setup(s, precision=C.LBM39_FP64, device=f"cuda:{local}")
+    fluid = int((s.mask == 0).sum())
+    out = {"workload": WORKLOADS["naca"], "cells": s.ncells, "fluid_cells": fluid}
+    L.step(args.warmup)
+    L.sync()
+    for name, t_start in (("early", args.warmup), ("developed", developed_at)):
+        while L.time < t_start:
+            L.step(min(500, t_start - L.time))
+            L.sync()
+        st0 = L.stats()
+        _, ms, clocks = timed_steps(L, args.steps, local)
+        L.sync()
+        st1 = L.stats()
+        sec = {"steps": [t_start, t_start + args.steps],
+               "mlups": round(s.ncells * args.steps / (ms * 1e-3) / 1e6, 3),
+               "fluid_mlups": round(fluid * args.steps / (ms * 1e-3) / 1e6, 3),
+               "ms_per_step": round(ms / args.steps, 4), "sm_mhz": clocks.get("sm_mhz")}
+        sec.update(counter_shares(st0, st1, fluid * args.steps))
+        out[name] = sec
+    L.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="naca", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="box256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -518,6 +670,15 @@ def main():
                     help="poly workload: lattice side n of the periodic n x n x 1 lattice")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision form: also run the FP64 path and report L1 error, drift, speedup")
+    ap.add_argument("--sections", default="precision,serving,airfoil",
+                    help="FP64 256^3 box line: comma-separated extra sections to run in the same "
+                         "line (precision, serving, airfoil), or 'none'")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving section of the 256^3 box line")
+    ap.add_argument("--serve-section-rate", type=float, default=3.0,
+                    help="arrival rate (Hz) of the serving section: saturating by default")
+    ap.add_argument("--developed-at", type=int, default=3000,
+                    help="airfoil section: first step of the developed-flow window")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -560,37 +721,19 @@ def main():
     fluid = st_init.fluid_cells
 
     L.step(args.warmup)
-    if L.sync() != 0:
-        raise RuntimeError("Newton failures during warm-up")
+    L.sync()
     st0 = L.stats()
-
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        evs[0].record(stream)
-        for k in range(args.steps):
-            L.step(1)
-            evs[k + 1].record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    clocks = clk.summary()
-    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    elapsed_s, units = reduce_over_ranks(evs[0].elapsed_time(evs[-1]) * 1e-3,
-                                         float(N * args.steps), dist, f"cuda:{local}")
+    per_step, _, clocks = timed_steps(L, args.steps, local, barrier)
+    elapsed_s, units = reduce_over_ranks(sum(per_step) * 1e-3, float(N * args.steps), dist,
+                                         f"cuda:{local}")
     elapsed_ms = elapsed_s * 1e3
-    if L.sync() != 0:
-        raise RuntimeError("Newton failures in the timed region")
+    L.sync()
     st1 = L.stats()
     cell_steps = fluid * args.steps
-    k_upd = (st1.newton_updates - st0.newton_updates) / cell_steps
-    # share of cell updates by Newton update count (0, 1, 2, 3, >= 4) and by branch of
-    # alpha(eps) (eps < 1e-2, < 1e-1, < 1, >= 1), over the timed steps
-    hist = [st1.newton_hist[k] - st0.newton_hist[k] for k in range(32)]
-    upd_share = [round(h / cell_steps, 4) for h in hist[:4]] + [round(sum(hist[4:]) / cell_steps, 4)]
-    eps_share = [round((st1.eps_hist[k] - st0.eps_hist[k]) / cell_steps, 4) for k in range(4)]
-    failed_share = round((st1.failed_cells - st0.failed_cells) / cell_steps, 6)
+    shares = counter_shares(st0, st1, cell_steps)
+    k_upd = shares["newton_updates_per_cell"]
     value = units / elapsed_s / 1e6
+    headline_state = L.read_numpy()
 
     # dominant kernel (the fused step): per-launch duration on its own stream
     step_ms = float(np.mean(per_step))
@@ -598,27 +741,29 @@ def main():
     rc, peak_tf = C.lbm39_selftest_dfma(scratch.data_ptr(), scratch.numel() * 8,
                                         stream.cuda_stream)
     C.check(rc, "lbm39_selftest_dfma")
+    del scratch
     # lattices one cell thick in z with u_z = 0 take the nine-constraint (z-mirror) solve
     reduced = (args.precision == "fp64" and s.nz == 1 and not np.any(s.u[2])
                and s.u_inf[2] == 0.0)
     model = FP64_FLOPS_MODEL["fp64_2d" if reduced else args.precision]
-    achieved_tf = None
-    if model is not None:
-        achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
+    achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
     hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
     traffic = None
     if NCU_TRAFFIC["kernel_hash"] == kernel_source_hash() and args.mach == 0.8:
         traffic = NCU_TRAFFIC["gb_per_launch"].get(f"{args.workload}/{args.precision}")
-    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4) if achieved_tf else None,
+    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4),
                 "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-                "frac": round(achieved_tf / peak_tf, 4) if achieved_tf else None,
+                "frac": round(achieved_tf / peak_tf, 4),
                 "traffic": round(traffic * 1e9) if traffic else None,
                 "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
                                "(of measured)",
-                "flops_per_cell_update": round(model[0] + model[1] * k_upd) if model else None,
+                "flops_per_cell_update": round(model[0] + model[1] * k_upd),
+                "flops_model": f"{model[0]:g} + {model[1]:g} x (Newton updates per cell), fitted "
+                               "to ncu FP64 instruction counts (2 per DFMA, 1 per DADD/DMUL)",
                 "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": HBM_PEAK_GBS,
                         "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),
-                        "bytes_per_update": BYTES_PER_UPDATE[args.precision]}}
+                        "bytes_per_update": BYTES_PER_UPDATE[args.precision],
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
 
     # end to end through the C ABI with host buffers: upload the initial fields from pinned
     # memory, then every step a step and a read-back of rho/u/T/p into pinned memory
@@ -642,33 +787,25 @@ def main():
                "h2d_bytes_per_step": int(5 * 8 * N / ke), "d2h_bytes_per_step": 6 * 8 * N,
                "steps": ke, "includes": "lbm39_init_host once (cold-start Newton) + per step "
                                        "lbm39_step(1) and lbm39_read_host of rho,u,T,p"}
+        del h_rho, h_u, h_T, h_out
+    launches = args.steps * (2 if L.has_fills else 1)
 
-    # precision form against the FP64 path on the same input and step count
+    # precision form against the FP64 path on the same input and step count (single run)
     form = None
     if args.compare_fp64 and prec == C.LBM39_MIXED:
-        mixed_state = L.read_numpy()
         st_end = L.stats()
+        L.close()
         Lf = Lattice.from_setup(s, precision=C.LBM39_FP64, device=f"cuda:{local}")
         Lf.step(args.warmup)
-        ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ef0.record(Lf.stream)
-        Lf.step(args.steps)
-        ef1.record(Lf.stream)
-        if Lf.sync() != 0:
-            raise RuntimeError("Newton failures in the FP64 comparison run")
+        _, ms, _ = timed_steps(Lf, args.steps, local)
         fp64_state = Lf.read_numpy()
-        fp64_mlups = N * args.steps / (ef0.elapsed_time(ef1) * 1e-3) / 1e6
+        fp64_mlups = N * args.steps / (ms * 1e-3) / 1e6
         Lf.close()
-        fl = s.mask == 0
-        (rm, um, Tm, _), (rf, uf, Tf, _) = mixed_state, fp64_state
-        l1 = [float(np.abs(rm[fl] - rf[fl]).mean() / np.abs(rf[fl]).mean()),
-              float(np.abs(um[:, fl] - uf[:, fl]).mean() / np.sqrt((uf[:, fl] ** 2).sum(0)).mean()),
-              float(np.abs(Tm[fl] - Tf[fl]).mean() / np.abs(Tf[fl]).mean())]
-        c0, c1 = np.array(st_init.conserved), np.array(st_end.conserved)
         nsteps = args.warmup + args.steps
-        drift = (np.abs(c1 - c0) / np.array([c0[0]] * 4 + [c0[4]])).tolist()
+        drift = drift_rel(st_init.conserved, st_end.conserved)
         form = {"compared_after_steps": nsteps,
-                "l1_rel_vs_fp64_rho_u_T": [float("%.3e" % v) for v in l1],
+                "l1_rel_vs_fp64_rho_u_T": [float("%.3e" % v)
+                                           for v in l1_rel(headline_state, fp64_state, s.mask == 0)],
                 "conservation_drift_rel_mass_mom_xyz_energy": [float("%.3e" % v) for v in drift],
                 "conservation_drift_per_1000_steps": [float("%.3e" % (v * 1000 / nsteps))
                                                       for v in drift],
@@ -676,6 +813,22 @@ def main():
                 "speedup_vs_fp64": round(value / fp64_mlups, 3),
                 "note": "FP64 path parity-checked against the FP64 oracle; mass and momentum "
                         "drift relative to the total mass"}
+    else:
+        L.close()
+    del L
+    torch.cuda.empty_cache()
+
+    # the other parts of the metric, in the same line as the FP64 256^3 box
+    sections = set() if args.sections == "none" else set(args.sections.split(","))
+    suite = (args.workload == "box256" and args.precision == "fp64" and world == 1)
+    serving = airfoil = None
+    if suite and "precision" in sections:
+        form = precision_form_section(args, local, s, (headline_state, value))
+    del headline_state
+    if suite and "airfoil" in sections:
+        airfoil = airfoil_section(args, local, args.developed_at)
+    if suite and "serving" in sections:
+        serving = serving_section(args, local, args.serve_requests, args.serve_section_rate)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -685,6 +838,13 @@ def main():
                "sample": f"{desc}: {done} oracle steps in {dt:.1f} s (after its cold-start init)"}
 
     if rank == 0:
+        config = {"workload": workload_text(args), "precision": args.precision,
+                  "cells": N, "fluid_cells": int(fluid),
+                  "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
+                  "l2": "inputs larger than L2 (%.2f GB of populations)" % (
+                      BYTES_PER_UPDATE[args.precision] / 2 * N / 1e9),
+                  "parallelism": "replicas" if world > 1 else "1 GPU"}
+        config.update(shares)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -692,24 +852,16 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32-storage/f64-solve",
             "data": "synthetic",
-            "config": {"workload": workload_text(args), "precision": args.precision,
-                       "cells": N, "fluid_cells": int(fluid),
-                       "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
-                       "newton_updates_per_cell": round(k_upd, 4),
-                       "newton_updates_share_0_1_2_3_4plus": upd_share,
-                       "alpha_branch_share": eps_share,
-                       "fallback_share": failed_share,
-                       "l2": "inputs larger than L2 (%.2f GB of populations)" % (
-                           BYTES_PER_UPDATE[args.precision] / 2 * N / 1e9),
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "config": config,
             "clocks": clocks, "roofline": roofline, "e2e": e2e,
-            "gpu_launches": args.steps * (2 if L.has_fills else 1),
+            "gpu_launches": launches,
             "cpu_baseline": cpu,
             "precision_form": form,
+            "serving": serving,
+            "airfoil": airfoil,
             "kernel_hash": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)
-    L.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -196,7 +196,12 @@ size_t lbm39_checkpoint_bytes(const lbm39_lattice* L);
 
 /* Copies the full state into / from a caller buffer of
  * lbm39_checkpoint_bytes bytes (host or device pointer).  A lattice loaded
- * from a checkpoint continues bit-identically to the one that saved it. */
+ * from a checkpoint continues bit-identically to the one that saved it, also
+ * when it is a newly created lattice.  The 256-byte header records the time,
+ * the lattice size (nx, ny, nz), the precision, a hash of the run parameters
+ * (every lbm39_params field except the size and init_maxit) and a hash of
+ * the mask; lbm39_load returns LBM39_ERR_ARG, and changes nothing, unless all
+ * of them match the loading lattice. */
 int lbm39_save(lbm39_lattice* L, void* buf);
 int lbm39_load(lbm39_lattice* L, const void* buf);
 
@@ -269,7 +274,8 @@ int lbm39_selftest_rcp(const double* x, double* y, double* ref, float* y32, floa
  * (with the device current), so make it before any stream capture.  Calls
  * share the array: calls that overlap on the GPU race.  Lattices of more than
  * 67,108,864 cells (8192 blocks of 8192 cells) are rejected with
- * LBM39_ERR_ARG.  The block decomposition differs from lbm39_stats', so the
+ * LBM39_ERR_ARG, and so is a call made while a device other than the one
+ * current at lbm39_create is current.  The block decomposition differs from lbm39_stats', so the
  * sums agree with it to rounding, not bit for bit. */
 int lbm39_conserved_noalloc(lbm39_lattice* L, double* sums5);
 

@@ -75,6 +75,37 @@ bool params_ok(const lbm39_params* p) {
   return true;
 }
 
+// 64-bit FNV-1a over a byte range, continued from h.
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// Hash of the run parameters a checkpoint's state depends on (everything in
+// lbm39_params except the lattice size, stored separately, and the Newton
+// budget of lbm39_init).
+uint64_t params_hash(const lbm39_params* p) {
+  uint64_t h = fnv1a(p->periodic, sizeof p->periodic);
+  h = fnv1a(&p->gamma, sizeof p->gamma, h);
+  h = fnv1a(&p->tau, sizeof p->tau, h);
+  h = fnv1a(&p->kn_sensor, sizeof p->kn_sensor, h);
+  h = fnv1a(&p->newton_tol, sizeof p->newton_tol, h);
+  h = fnv1a(&p->newton_maxit, sizeof p->newton_maxit, h);
+  h = fnv1a(&p->newton_min_upd, sizeof p->newton_min_upd, h);
+  h = fnv1a(&p->precision, sizeof p->precision, h);
+  h = fnv1a(&p->ref_rho, sizeof p->ref_rho, h);
+  h = fnv1a(&p->ref_T, sizeof p->ref_T, h);
+  h = fnv1a(&p->rho_inf, sizeof p->rho_inf, h);
+  h = fnv1a(p->u_inf, sizeof p->u_inf, h);
+  h = fnv1a(&p->T_inf, sizeof p->T_inf, h);
+  h = fnv1a(&p->reduce_2d, sizeof p->reduce_2d, h);
+  return h;
+}
+
 }  // namespace
 
 struct lbm39_lattice {
@@ -88,6 +119,8 @@ struct lbm39_lattice {
   bool fills = false;   // ghosts or solids: the fill kernels run after each pass
   bool mixed = false;
   cudaStream_t stream = nullptr;
+  int device = -1;               // the CUDA device current at lbm39_create
+  uint64_t mask_hash = 0;        // FNV-1a of the mask bytes (0 without a mask)
   long long t = 0;
   bool initialized = false;
   Desc desc{};
@@ -248,16 +281,22 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   long long fluid = N;
   bool ghosts = false, solids = false;
+  uint64_t mask_hash = 0;
   if (mask_dev) {
     std::vector<uint8_t> m(N);
     CUDA_OK(cudaMemcpyAsync(m.data(), mask_dev, N, cudaMemcpyDeviceToHost, stream));
     CUDA_OK(cudaStreamSynchronize(stream));
     const int rc = check_mask(p, m, &fluid, &ghosts, &solids);
     if (rc) return rc;
+    mask_hash = fnv1a(m.data(), m.size());
   }
+  int device = -1;
+  CUDA_OK(cudaGetDevice(&device));
   lbm39_lattice* L = new (std::nothrow) lbm39_lattice;
   if (!L) return LBM39_ERR_ARG;
   L->p = *p;
+  L->device = device;
+  L->mask_hash = mask_hash;
   L->N = N;
   L->Np = plane_stride(N);
   L->fluid = fluid;
@@ -555,6 +594,11 @@ int lbm39_save(lbm39_lattice* L, void* buf) {
   hdr[2] = (uint64_t)L->N;
   hdr[3] = (uint64_t)L->p.precision;
   hdr[4] = (uint64_t)L->desc.d2;
+  hdr[5] = (uint64_t)L->p.nx;
+  hdr[6] = (uint64_t)L->p.ny;
+  hdr[7] = (uint64_t)L->p.nz;
+  hdr[8] = params_hash(&L->p);
+  hdr[9] = L->mask_hash;
   char* b = static_cast<char*>(buf);
   const size_t pb = L->pop_bytes(), lb = sizeof(double) * SOLVER_PLANES * L->Np;
   CUDA_OK(cudaMemcpyAsync(b, hdr, sizeof hdr, cudaMemcpyDefault, L->stream));
@@ -570,7 +614,9 @@ int lbm39_load(lbm39_lattice* L, const void* buf) {
   const char* b = static_cast<const char*>(buf);
   CUDA_OK(cudaMemcpyAsync(hdr, b, sizeof hdr, cudaMemcpyDefault, L->stream));
   CUDA_OK(cudaStreamSynchronize(L->stream));
-  if (hdr[0] != CKPT_MAGIC || hdr[2] != (uint64_t)L->N || hdr[3] != (uint64_t)L->p.precision)
+  if (hdr[0] != CKPT_MAGIC || hdr[2] != (uint64_t)L->N || hdr[3] != (uint64_t)L->p.precision ||
+      hdr[5] != (uint64_t)L->p.nx || hdr[6] != (uint64_t)L->p.ny || hdr[7] != (uint64_t)L->p.nz ||
+      hdr[8] != params_hash(&L->p) || hdr[9] != L->mask_hash)
     return LBM39_ERR_ARG;
   const size_t pb = L->pop_bytes(), lb = sizeof(double) * SOLVER_PLANES * L->Np;
   CUDA_OK(cudaMemcpyAsync(L->pop, b + 256, pb, cudaMemcpyDefault, L->stream));
@@ -886,6 +932,9 @@ int lbm39_conserved_noalloc(lbm39_lattice* L, double* sums5) {
   if (!L || !sums5) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   if (L->N > (long long)NOALLOC_BLOCKS_MAX * NOALLOC_CELLS_PER_BLOCK) return LBM39_ERR_ARG;
+  int cur = -1;
+  CUDA_OK(cudaGetDevice(&cur));
+  if (cur != L->device) return LBM39_ERR_ARG;  // the scratch looked up must be the lattice's
   int rc = LBM39_OK;
   double* scratch = noalloc_scratch(&rc);
   if (!scratch) return rc;

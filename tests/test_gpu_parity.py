@@ -154,6 +154,53 @@ def test_checkpoint_resume_is_bit_identical(Lat):
         assert np.array_equal(x, y)
 
 
+def test_checkpoint_restores_into_a_new_lattice(Lat):
+    """A checkpoint loaded into a newly created lattice of the same shape, parameters and mask
+    (here the small airfoil: bounce-back, freestream and outflow cells) continues bit for bit
+    like the lattice that saved it."""
+    s = inputs.naca(nx=96, ny=48, chord=24, x_le=24)
+    L = Lat.from_setup(s)
+    L.step(7)
+    buf = L.checkpoint()
+    L.step(5)
+    a = L.read_numpy()
+    L2 = Lat.from_setup(s)
+    L2.restore(buf)
+    assert L2.time == 7
+    L2.step(5)
+    b = L2.read_numpy()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_checkpoint_of_another_lattice_is_rejected(Lat):
+    """lbm39_load rejects a checkpoint whose lattice differs from the loading one: another
+    shape with the same cell count, another relaxation time, another mask; the loading
+    lattice's state is left as it was."""
+    from paper_1910_13515_gb300 import lbm39 as C
+    s = box_with_obstacle(seed=5, shape=(8, 10, 12))
+    L = Lat.from_setup(s)
+    L.step(3)
+    buf = L.checkpoint()
+    others = []
+    t = inputs.box(seed=5, shape=(12, 10, 8))  # same N, transposed shape
+    others.append(Lat.from_setup(t))
+    others.append(Lat.from_setup(s, tau=s.tau + 0.01))
+    m = s.mask.copy()
+    m[0] = 1 - m[0]
+    u = inputs.box(seed=5, shape=(8, 10, 12))
+    u.mask = m
+    others.append(Lat.from_setup(u))
+    for Lo in others:
+        before = Lo.read_numpy()
+        with pytest.raises(C.LBM39Error) as e:
+            Lo.restore(buf)
+        assert e.value.code == C.LBM39_ERR_ARG
+        after = Lo.read_numpy()
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+
+
 def test_host_io_matches_device_io(Lat):
     s = inputs.naca(nx=64, ny=32, chord=16, x_le=16)
     L1 = Lat.from_setup(s)
