@@ -90,6 +90,18 @@ typedef struct {
                                z-even constraints (the others are exactly zero there):
                                the same values, less work.  0: always all 13.  The
                                precision form always solves all 13. */
+  double prandtl;           /* Prandtl number (Sec. 3 leaves its adjustment out: Pr = 1).
+                               1 (default) or 0: the paper's BGK collision.  Otherwise a
+                               quasi-equilibrium collision with two relaxation times: f
+                               relaxes by BGK with tau_eff = tau alpha(eps); g relaxes
+                               with tau_eff towards g^eq and, with 1/tau_eff - 1/tau2,
+                               towards g^eq_i (1 + c_i . b), c_i = xi_i - u, b = 2 q /
+                               ((2 C_v - D) rho T^2), q = (1/2) sum_i c_i (|c_i|^2 f_i +
+                               g_i) the heat flux; so the heat flux relaxes with tau2 =
+                               1/2 + (tau_eff - 1/2)/Pr and the stress with tau_eff, and
+                               Pr = (tau_eff - 1/2)/(tau2 - 1/2).  Mass, momentum and
+                               energy are conserved as before.  Range [0.01, 100];
+                               needs 2 C_v - D > 0 (gamma < 5/3). */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;
@@ -108,7 +120,7 @@ typedef struct {
 
 /* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice
  * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 0,
- * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5)). */
+ * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5), reduce_2d 1, Pr 1). */
 void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* The compiled D3Q39 velocity set (Sec. 3: (0,0,0), (1,0,0)_FS, (+-1,+-1,+-1),
@@ -228,7 +240,9 @@ int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precisio
 
 /* Makes lattices[0..n) the resident set; lattice j steps until its time
  * reaches t_end[j] (>= its current time).  Lattices must be initialised, of
- * the batch's precision, and stay alive while resident.  Synchronous. */
+ * the batch's precision, with Pr = 1 (lbm39_params.prandtl 1 or 0; other
+ * lattices are rejected with LBM39_ERR_ARG), and stay alive while resident.
+ * Synchronous. */
 int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_t* t_end,
                     int32_t n);
 

@@ -39,6 +39,7 @@ typedef struct {
   int32_t newton_maxit;
   int32_t newton_min_upd; /* reading: at least this many updates per solve */
   double rho_inf, u_inf[3], T_inf; /* far-field state for freestream cells */
+  double prandtl;      /* Prandtl number; 0 or 1: Pr = 1, plain BGK (Sec. 3) */
 } o39_params;
 
 typedef struct {
@@ -544,9 +545,60 @@ void o39_cell_macros(const o39_params *p, const double *f, const double *g,
   *T_out = (e2 - rho * u2) / (2.0 * cv * rho);
 }
 
+/* Prandtl-number adjustment (Sec. 3 names it -- a quasi-equilibrium, or a
+ * temperature-scaled collision -- and leaves it out, so that Pr = 1; the
+ * formulas here are this oracle's reading, written from the mathematics).
+ *
+ * Quasi-equilibrium collision with two relaxation times: each population
+ * relaxes towards a quasi-equilibrium h* with 1/tau and h* towards h^eq with
+ * 1/tau2,
+ *   h' = h - (h - h^eq)/tau + (1/tau - 1/tau2) (h* - h^eq),   h = f, g.
+ * The quasi-equilibrium keeps f* = f^eq and differs from the equilibrium only
+ * in the heat flux, which it takes from the current populations: with the
+ * peculiar velocity c_i = xi_i - u, the heat flux is
+ *   q = (1/2) sum_i c_i (|c_i|^2 f_i + g_i),
+ * which is zero at the 13-moment equilibrium (its contracted third moment is
+ * the Maxwellian's, Eq. 13constraints, and sum_i c_i g^eq_i = 0), and
+ *   g*_i - g^eq_i = dg_i = g^eq_i (c_i . b),  b = 2 q / ((2 C_v - D) rho T^2),
+ * so that (1/2) sum_i c_i dg_i = q (because sum_i f^eq_i c_i c_i = rho T I at
+ * the equilibrium), while sum_i dg_i = 0 (no energy moves) and f is not
+ * touched (mass and momentum untouched).  After one collision the heat flux is
+ * (1 - 1/tau2) q and the stress relaxes with 1/tau as before, so to first
+ * order in the Chapman-Enskog expansion the viscosity goes with (tau - 1/2)
+ * and the heat conductivity with (tau2 - 1/2): Pr = (tau - 1/2)/(tau2 - 1/2).
+ * reading: tau2 follows the relaxation time actually used, tau_eff = tau
+ * alpha(eps), as tau2 = 1/2 + (tau_eff - 1/2)/Pr, so the sensor of Eq. (alpha)
+ * keeps the Prandtl number.  Needs 2 C_v - D > 0 (g^eq nonzero). */
+static double heat_flux_tau(const o39_params *p, double tau_eff) {
+  if (p->prandtl == 0.0 || p->prandtl == 1.0) return tau_eff;
+  return 0.5 + (tau_eff - 0.5) / p->prandtl;
+}
+
+static void prandtl_correction(const o39_params *p, const double *f, const double *g,
+                               const double *geq, double rho, const double *u, double T,
+                               double *dg) {
+  for (int i = 0; i < Q; ++i) dg[i] = 0.0;
+  if (p->prandtl == 0.0 || p->prandtl == 1.0) return;
+  double cv = 1.0 / (p->gamma - 1.0);
+  double q[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < Q; ++i) {
+    double c[3] = {VEL[i][0] - u[0], VEL[i][1] - u[1], VEL[i][2] - u[2]};
+    double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    for (int a = 0; a < DIM; ++a) q[a] += 0.5 * c[a] * (c2 * f[i] + g[i]);
+  }
+  double b[3];
+  for (int a = 0; a < DIM; ++a) b[a] = 2.0 * q[a] / ((2.0 * cv - DIM) * rho * T * T);
+  for (int i = 0; i < Q; ++i) {
+    double cb = 0.0;
+    for (int a = 0; a < DIM; ++a) cb += (VEL[i][a] - u[a]) * b[a];
+    dg[i] = geq[i] * cb;
+  }
+}
+
 /* One BGK collision of one fluid cell (Sec. 3 and Eq. DeltaAvg / alpha):
  * macros -> MB targets -> Newton (warm start lam) -> f^eq, g^eq = (2C_v-D) T f^eq
- * -> eps, alpha -> h* = h - (h - h^eq)/(tau alpha) for h = f and h = g.
+ * -> eps, alpha -> h* = h - (h - h^eq)/(tau alpha) for h = f and h = g
+ * (with the Prandtl-number adjustment above when p->prandtl is not 1).
  * t: the time step being taken; on_fb: the cell's "on the fallback" flag (in
  * and out), which with t decides the solve's budget (failure policy above).
  * reading: eps uses f only and the same alpha relaxes f and g (Pr = 1).
@@ -585,9 +637,12 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, uin
   eps /= Q;
   double alpha = p->kn_sensor ? o39_alpha(eps, p->tau) : 1.0;
   double tau_eff = p->tau * alpha;
+  double dg[Q];
+  prandtl_correction(p, f, g, geq, rho, u, T, dg);
+  double tau2 = heat_flux_tau(p, tau_eff);
   for (int i = 0; i < Q; ++i) {
     f[i] = f[i] - (f[i] - feq[i]) / tau_eff;
-    g[i] = g[i] - (g[i] - geq[i]) / tau_eff;
+    g[i] = g[i] - (g[i] - geq[i]) / tau_eff + (1.0 / tau_eff - 1.0 / tau2) * dg[i];
   }
   if (eps_out) *eps_out = eps;
   if (alpha_out) *alpha_out = alpha;

@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("rho_inf", ctypes.c_double),
         ("u_inf", ctypes.c_double * 3),
         ("T_inf", ctypes.c_double),
+        ("prandtl", ctypes.c_double),
     ]
 
 
@@ -226,6 +227,7 @@ class Config:
     u_inf: tuple = (0.0, 0.0, 0.0)
     T_inf: float = 0.5
     init_maxit: int = 200
+    prandtl: float = 1.0
 
     def params(self) -> Params:
         p = Params()
@@ -241,6 +243,7 @@ class Config:
         p.newton_min_upd = int(self.newton_min_upd)
         p.rho_inf = self.rho_inf
         p.T_inf = self.T_inf
+        p.prandtl = self.prandtl
         return p
 
     @property

@@ -47,6 +47,8 @@ struct Phys {
   int kn_sensor;    // Eq. (alpha) on/off
   double omega[4];  // 1 / (tau alpha) for the four branches of Eq. (alpha) (1/tau without
                     // the sensor), formed on the host with IEEE division
+  int pr_adjust;    // Prandtl-number adjustment on (Pr != 1)
+  double domega[4]; // per branch: 1/tau_eff - 1/tau2, tau2 = 1/2 + (tau_eff - 1/2)/Pr
 };
 
 // Reciprocals without the IEEE division sequence.
@@ -562,6 +564,12 @@ __device__ __forceinline__ double omega_of(const Phys& ph, int branch) {
                                                                             : ph.omega[3];
 }
 
+// 1/tau_eff - 1/tau2 of that branch (Prandtl-number adjustment).
+__device__ __forceinline__ double domega_of(const Phys& ph, int branch) {
+  return branch == 0 ? ph.domega[0] : branch == 1 ? ph.domega[1] : branch == 2 ? ph.domega[2]
+                                                                              : ph.domega[3];
+}
+
 // FP32 screen of s = 39 eps = sum_i |f_i - f^eq_i| / f^eq_i (Eq. DeltaAvg).  With
 // u = 2^-24: each float view (f~, F~, rho~) is within 2u of its double, q = rho~ F~
 // adds u, the difference u, rcp32 2u and the product u, so each term is within
@@ -579,6 +587,21 @@ __device__ __forceinline__ bool screen_undecided(float s39, int emin, int emax, 
       !(rho32 >= 0x1p-20f && rho32 <= 0x1p20f))
     return true;
   const float band = 3e-5f + 3e-6f * s39;
+  return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;
+}
+
+// The same screen in the precision form, where the FP32 terms are |d_i| r_i with
+// d_i = f~_i - rf_i (stored deviation minus rf_i = f^eq_i - f_ref_i rounded to float)
+// and r_i = rcp32(rho~ F~_i).  With u = 2^-24: rf_i is within u|rf_i| of its FP64 value
+// and d_i within u|d_i| of f~_i - rf_i, so |d_i| is within u(|d_i| + |rf_i|) of
+// |f_i - f^eq_i|; r_i is within 7u of 1/f^eq_i (two float views 2u each, the product u,
+// rcp32 2u) and the product adds u; four interleaved partial sums of at most 10 terms
+// add at most 12u s.  In all |s32 - s| <= u (1.01 b + 22 s32) with b = sum_i |rf_i| r_i.
+// True when s32 or b is not finite (a view out of float's range makes r_i infinite), or
+// when s32 lies within 4u (b + 22 s32) (about twice the bound) of a threshold.
+__device__ __forceinline__ bool screen_undecided_dev(float s39, float b) {
+  if (!(s39 < 1e30f) || !(b < 1e30f)) return true;
+  const float band = 0x1p-22f * (b + 22.0f * s39);
   return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;
 }
 

@@ -190,7 +190,9 @@ __device__ __forceinline__ float round_float(double x) {
 // Phase C: gather again, Knudsen sensor (Eq. DeltaAvg, f only), tau_eff =
 // tau alpha(eps) (Eq. alpha) for f and g, BGK and push.  F holds the final
 // normalised equilibrium; f^eq = rho F, g^eq = (2C_v - D) T rho F.
-template <bool ODD, class P, int BLK>
+// PR: with the Prandtl-number adjustment (the quasi-equilibrium correction of g;
+// a separate instantiation, so the paper's Pr = 1 collision carries none of it).
+template <bool ODD, class P, int BLK, bool PR = false>
 __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const Nbr& nb,
                                           const Macro& M, WS<BLK> F) {
   const Phys& ph = d.ph;
@@ -225,31 +227,86 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
       }
       eps = s * (1.0 / Q);
     }
-    const double omega = omega_of(ph, alpha_branch(eps));
+    const int branch = alpha_branch(eps);
+    const double omega = omega_of(ph, branch);
     static_for<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       push<ODD, P, i>(d, cell, nb, 0, fma(-omega, fma(-rho, F[i], f[i]), f[i]));
     });
+    double s13[NM];
+    if constexpr (PR) gen::moments_s<double>(f, s13);  // sum_i f_i phi_k(xi_i)
     P g[Q];
     gather<ODD, P>(d, cell, nb, Q, g);
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      push<ODD, P, i>(d, cell, nb, Q, fma(-omega, fma(-cgr, F[i], g[i]), g[i]));
-    });
+    if constexpr (!PR) {
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        push<ODD, P, i>(d, cell, nb, Q, fma(-omega, fma(-cgr, F[i], g[i]), g[i]));
+      });
+    } else {
+      // heat flux q = (1/2) sum_i c_i (|c_i|^2 f_i + g_i), c_i = xi_i - u, from the raw
+      // sums: sum_i f_i c_i |c_i|^2 = S3 - 2 S2 u - u sum_i f_i |xi_i|^2 + 2 rho u |u|^2
+      const double ux = M.ux, uy = M.uy, uz = M.uz, u2 = ux * ux + uy * uy + uz * uz;
+      const double e2f = s13[4] + s13[5] + s13[6];
+      double g0 = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
+        g0 += g[i];
+        if constexpr (cx != 0) gx = fma((double)cx, g[i], gx);
+        if constexpr (cy != 0) gy = fma((double)cy, g[i], gy);
+        if constexpr (cz != 0) gz = fma((double)cz, g[i], gz);
+      });
+      const double r2u2 = 2.0 * s13[0] * u2;
+      const double qx = 0.5 * (s13[10] - 2.0 * (s13[4] * ux + s13[7] * uy + s13[8] * uz) -
+                               ux * e2f + r2u2 * ux + gx - ux * g0);
+      const double qy = 0.5 * (s13[11] - 2.0 * (s13[7] * ux + s13[5] * uy + s13[9] * uz) -
+                               uy * e2f + r2u2 * uy + gy - uy * g0);
+      const double qz = 0.5 * (s13[12] - 2.0 * (s13[8] * ux + s13[9] * uy + s13[6] * uz) -
+                               uz * e2f + r2u2 * uz + gz - uz * g0);
+      // (1/tau - 1/tau2) g^eq_i (c_i . b), b = 2 q / ((2 C_v - D) rho T^2),
+      // = F_i (beta0 + xi_i . beta) with beta = 2 (1/tau - 1/tau2) q / T, beta0 = -u . beta
+      const double k = 2.0 * domega_of(ph, branch) / M.T;
+      const double bx = k * qx, by = k * qy, bz = k * qz;
+      const double b0 = -(ux * bx + uy * by + uz * bz);
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
+        const double cb = fma((double)cx, bx, fma((double)cy, by, fma((double)cz, bz, b0)));
+        push<ODD, P, i>(d, cell, nb, Q,
+                        fma(F[i], cb, fma(-omega, fma(-cgr, F[i], g[i]), g[i])));
+      });
+    }
   } else {
     // precision form: h~ = h - h_ref stored in FP32; equilibrium deviation
     // h^eq - h_ref formed in FP64 and rounded; sensor and BGK in FP32.
+    // FP32 screen of s = 39 eps with its own error scale (screen_undecided_dev); the FP64
+    // value of the stored state where the screen cannot decide the branch of Eq. (alpha)
     const double* __restrict__ href = d.href;
     P f[Q];
     gather<ODD, P>(d, cell, nb, 0, f);
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ref[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double Fi = F[i];
-      f[i] -= round_float(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
-      acc[i & 3] += fabsf(f[i]) * rcp32(rho32 * trunc_float(Fi));
+      const float rf = round_float(fma(rho, Fi, -__ldg(href + i)));  // f^eq - f_ref
+      f[i] -= rf;                                                     // f - f^eq
+      const float r = rcp32(rho32 * trunc_float(Fi));
+      acc[i & 3] += fabsf(f[i]) * r;
+      ref[i & 3] += fabsf(rf) * r;
     }
-    eps = (double)((acc[0] + acc[1]) + (acc[2] + acc[3])) * (1.0 / Q);
+    const float s32 = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    eps = (double)s32 * (1.0 / Q);
+    if (screen_undecided_dev(s32, (ref[0] + ref[1]) + (ref[2] + ref[3]))) {
+      P fs[Q];
+      gather<ODD, P>(d, cell, nb, 0, fs);  // the stored values (cached)
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double feq = rho * F[i];
+        s += fabs((exact_double(fs[i]) + __ldg(href + i)) - feq) / feq;
+      }
+      eps = s * (1.0 / Q);
+    }
     const float omega = (float)omega_of(ph, alpha_branch(eps));
     P f2[Q];
     gather<ODD, P>(d, cell, nb, 0, f2);  // the stored values again (cached)
@@ -259,11 +316,36 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     });
     P g[Q];
     gather<ODD, P>(d, cell, nb, Q, g);
-    static_for<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const float qg = round_float(fma(cgr, F[i], -__ldg(href + Q + i)));
-      push<ODD, P, i>(d, cell, nb, Q, fmaf(-omega, g[i] - qg, g[i]));
-    });
+    if constexpr (!PR) {
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const float qg = round_float(fma(cgr, F[i], -__ldg(href + Q + i)));
+        push<ODD, P, i>(d, cell, nb, Q, fmaf(-omega, g[i] - qg, g[i]));
+      });
+    } else {
+      // heat flux from the non-equilibrium parts (the 13-moment equilibrium has none):
+      // q = (1/2) sum_i c_i (|c_i|^2 (f_i - f^eq_i) + (g_i - g^eq_i)), in FP32
+      const float ux = (float)M.ux, uy = (float)M.uy, uz = (float)M.uz;
+      float e[Q], qx = 0.0f, qy = 0.0f, qz = 0.0f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        e[i] = g[i] - round_float(fma(cgr, F[i], -__ldg(href + Q + i)));  // g - g^eq
+        const float cx = (float)kCX[i] - ux, cy = (float)kCY[i] - uy, cz = (float)kCZ[i] - uz;
+        const float w = 0.5f * fmaf(cx * cx + cy * cy + cz * cz, f[i], e[i]);
+        qx = fmaf(cx, w, qx);
+        qy = fmaf(cy, w, qy);
+        qz = fmaf(cz, w, qz);
+      }
+      const float k = (float)(2.0 * domega_of(ph, alpha_branch(eps)) / M.T);
+      const float bx = k * qx, by = k * qy, bz = k * qz;
+      const float b0 = -(ux * bx + uy * by + uz * bz);
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = CX[i], cy = CY[i], cz = CZ[i];
+        const float cb = fmaf((float)cx, bx, fmaf((float)cy, by, fmaf((float)cz, bz, b0)));
+        push<ODD, P, i>(d, cell, nb, Q, fmaf(trunc_float(F[i]), cb, fmaf(-omega, e[i], g[i])));
+      });
+    }
   }
   return alpha_branch(eps);
 }
@@ -345,7 +427,7 @@ __device__ __forceinline__ int retry_budget(long long t) {
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 // D2: the nine-function constraint system of a z-mirror-symmetric lattice one
 // cell thick in z (Sys<true>; the same values as the full system).
-template <bool ODD, class P, int BLK, bool D2 = false>
+template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
@@ -362,7 +444,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
-  const int branch = relax_push<ODD, P, BLK>(d, cell, fresh_nbr<ODD>(d, c), M, F);
+  const int branch = relax_push<ODD, P, BLK, PR>(d, cell, fresh_nbr<ODD>(d, c), M, F);
   atomicAdd(&s_ctr[CTR_FAILED], (unsigned)nr.failed);
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
   atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
@@ -370,7 +452,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
 }
 
 // One time step over every fluid cell (even or odd AA pass).
-template <bool ODD, class P, int BLK, bool D2>
+template <bool ODD, class P, int BLK, bool D2, bool PR = false>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
@@ -378,7 +460,7 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
   if (cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID))
-    step_cell<ODD, P, BLK, D2>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
+    step_cell<ODD, P, BLK, D2, PR>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 

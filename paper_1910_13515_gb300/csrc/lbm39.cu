@@ -18,6 +18,7 @@
 #include "batch.cuh"
 #include "kernels.cuh"
 #include "lattice_view.h"
+#include "prandtl.h"
 
 using namespace lbm39;
 
@@ -68,6 +69,9 @@ bool params_ok(const lbm39_params* p) {
   if (p->precision != LBM39_FP64 && p->precision != LBM39_MIXED) return false;
   if (p->reduce_2d != 0 && p->reduce_2d != 1) return false;
   if (p->precision == LBM39_MIXED && !(p->ref_rho > 0.0 && p->ref_T > 0.0)) return false;
+  if (!(p->prandtl == 0.0 || p->prandtl == 1.0 ||
+        (p->prandtl >= 0.01 && p->prandtl <= 100.0 && 2.0 / (p->gamma - 1.0) - D > 0.0)))
+    return false;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? p->nx : a == 1 ? p->ny : p->nz;
     if (!p->periodic[a] && n < 7) return false;  // 3 boundary layers per end + fluid
@@ -103,6 +107,7 @@ uint64_t params_hash(const lbm39_params* p) {
   h = fnv1a(p->u_inf, sizeof p->u_inf, h);
   h = fnv1a(&p->T_inf, sizeof p->T_inf, h);
   h = fnv1a(&p->reduce_2d, sizeof p->reduce_2d, h);
+  h = fnv1a(&p->prandtl, sizeof p->prandtl, h);
   return h;
 }
 
@@ -145,6 +150,14 @@ struct Launch {
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
     // the reduced (z-mirror) system serves the FP64 path only (see reduction_allowed)
     constexpr bool fp64 = sizeof(P) == 8;
+    if (L->desc.ph.pr_adjust) {  // Prandtl-number adjustment (prandtl.cu)
+      launch_step_prandtl(L->desc, odd, !fp64, L->stream);
+      if (L->fills) {
+        if (odd) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+        else k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+      }
+      return;
+    }
     if (!odd) {
       if (fp64 && L->desc.d2) k_step<false, P, BLK, fp64><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
       else k_step<false, P, BLK, false><<<grid, BLK, WS_BYTES, L->stream>>>(L->desc);
@@ -195,6 +208,7 @@ void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz) {
   p->ref_rho = 1.0; p->ref_T = 0.5;
   p->rho_inf = 1.0; p->T_inf = 0.5;
   p->reduce_2d = 1;
+  p->prandtl = 1.0;
 }
 
 int lbm39_velocities(int32_t* vel, double* w) {
@@ -330,7 +344,14 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   d.ph.kn_sensor = p->kn_sensor ? 1 : 0;
   {
     const double alpha[4] = {1.0, 1.05, 1.35, 1.0 / p->tau};  // Eq. (alpha)
-    for (int b = 0; b < 4; ++b) d.ph.omega[b] = 1.0 / (p->tau * (p->kn_sensor ? alpha[b] : 1.0));
+    d.ph.pr_adjust = !(p->prandtl == 0.0 || p->prandtl == 1.0);
+    for (int b = 0; b < 4; ++b) {
+      const double tau_eff = p->tau * (p->kn_sensor ? alpha[b] : 1.0);
+      d.ph.omega[b] = 1.0 / tau_eff;
+      // Prandtl-number adjustment: the heat flux relaxes with tau2
+      const double tau2 = d.ph.pr_adjust ? 0.5 + (tau_eff - 0.5) / p->prandtl : tau_eff;
+      d.ph.domega[b] = 1.0 / tau_eff - 1.0 / tau2;
+    }
   }
   int rc = LBM39_OK;
   // reference populations of the precision form and their moments
@@ -414,7 +435,8 @@ static int init_begin(lbm39_lattice* L) {
 // forms the z-odd pivots and may reject a direction over one of them, which
 // the reduced system would not, so the two would not give the same values.
 static bool reduction_allowed(const lbm39_lattice* L) {
-  return L->p.reduce_2d == 1 && L->p.nz == 1 && L->p.u_inf[2] == 0.0 && !L->mixed;
+  return L->p.reduce_2d == 1 && L->p.nz == 1 && L->p.u_inf[2] == 0.0 && !L->mixed &&
+         !L->desc.ph.pr_adjust;
 }
 
 // After the init kernels: waits for them and fixes the constraint system.
@@ -787,6 +809,7 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
     if (!L) return LBM39_ERR_ARG;
     if (!L->initialized) return LBM39_ERR_STATE;
     if (L->p.precision != B->precision || t_end[j] < L->t) return LBM39_ERR_ARG;
+    if (L->desc.ph.pr_adjust) return LBM39_ERR_ARG;  // the packed step is the Pr = 1 collision
     cells += L->N;
   }
   if (cells > B->maxcells) return LBM39_ERR_ARG;

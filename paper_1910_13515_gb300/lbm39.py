@@ -45,6 +45,7 @@ class lbm39_params(ctypes.Structure):
         ("ref_rho", ctypes.c_double), ("ref_T", ctypes.c_double),
         ("rho_inf", ctypes.c_double), ("u_inf", ctypes.c_double * 3), ("T_inf", ctypes.c_double),
         ("reduce_2d", ctypes.c_int32),
+        ("prandtl", ctypes.c_double),
     ]
 
 

@@ -311,25 +311,42 @@ def test_cells_outside_the_cone_take_the_fallback(Lat):
         assert max(d) <= TOL, (n, d)
 
 
-def test_naca_with_developing_fallback_cells_parity(Lat):
-    """A small NACA0012 lattice at Ma 2.0 (u_inf = 1.67 at T_inf = 0.5): from step ~10 the flow
-    reaches states outside the 13-moment cone, and by step 40 several hundred cells are on the
-    fallback, retrying the full solve on steps 8, 16, 24 and 32.  The GPU matches the oracle to
-    1e-11, with the same failure count and the same cells flagged on the fallback."""
-    s = inputs.naca(nx=96, ny=48, chord=24, x_le=24, mach=2.0)
-    n = 40
-    L, g, fg = gpu_run(Lat, s, n)
-    st, fo = run_oracle(s, n)
-    assert fo > 1000 and fg == fo
-    d = rel_diffs(g, o.macros(st), s.mask, s.gamma)
-    assert max(d) <= TOL, d
+def _gpu_flags(L, ncells):
     buf = L.checkpoint()
-    Np = (s.ncells + 63) // 64 * 64
-    lam = buf[256:].view(torch.float64)[78 * Np: 91 * Np].view(13, Np)[:, :s.ncells]
-    flags = fallback_flags(lam.T.contiguous().cpu().numpy())
+    Np = (ncells + 63) // 64 * 64
+    lam = buf[256:].view(torch.float64)[78 * Np: 91 * Np].view(13, Np)[:, :ncells]
+    return fallback_flags(lam.T.contiguous().cpu().numpy())
+
+
+def test_naca_with_developing_fallback_cells_parity(Lat):
+    """A small NACA0012 lattice at Ma 2.0 (u_inf = 1.67 at T_inf = 0.5): from step ~8 the flow
+    reaches states outside the 13-moment cone, and by step 40 several hundred cells are on the
+    fallback, retrying the full solve on steps 0, 8, 16, 24 and 32.  Up to step 17 the GPU
+    matches the oracle to 1e-11.  Later the cells next to the cone's boundary, where the
+    constraint Jacobian is nearly singular, amplify round-off: the oracle run from an initial
+    state perturbed by 1e-15 differs from the unperturbed one by ~4e-8 in u at step 40.  There
+    the GPU must agree with the oracle within 10x that self-difference.  At both times the
+    failure counts are equal and the same cells are flagged on the fallback."""
+    s = inputs.naca(nx=96, ny=48, chord=24, x_le=24, mach=2.0)
     fl = s.mask == 0
-    assert st.on_fb[fl].sum() > 100
-    assert np.array_equal(flags[fl], st.on_fb[fl])
+    L = Lat.from_setup(s)
+    cfg = oracle_cfg(s)
+    st = o.init(cfg, s.mask, s.rho, s.u, s.T)
+    pert = o.init(cfg, s.mask, s.rho, s.u, s.T)
+    pert.f *= 1 + 1e-15 * np.random.default_rng(0).uniform(-1, 1, pert.f.shape)
+    for n, floor in ((17, 0.0), (40, None)):
+        L.step(n - st.t)
+        fg = L.sync()
+        o.step(st, n - st.t)
+        o.step(pert, n - pert.t)
+        fo = st.stats.failed_cells
+        assert fo > 100 and fg == fo, (n, fg, fo)
+        assert np.array_equal(_gpu_flags(L, s.ncells)[fl], st.on_fb[fl]) and st.on_fb[fl].sum() > 20
+        d = rel_diffs(L.read_numpy(), o.macros(st), s.mask, s.gamma)
+        self_d = rel_diffs(o.macros(pert), o.macros(st), s.mask, s.gamma)
+        tol = TOL if floor is not None else 10 * max(self_d)
+        assert max(self_d) < (TOL if floor is not None else 1e-6), (n, self_d)
+        assert max(d) <= tol, (n, d, self_d)
 
 
 def test_unrealisable_state_is_reported_not_faulted(Lat):

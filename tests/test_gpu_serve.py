@@ -1,5 +1,6 @@
 """Serving form on the GPU: requests run together through packed, graph-replayed steps give
-exactly (bit for bit) what each gives alone through lbm39_step."""
+exactly (bit for bit) what each gives alone through lbm39_step, and the served FP64 results
+match the FP64 CPU oracle."""
 import numpy as np
 import pytest
 
@@ -47,3 +48,28 @@ def test_served_results_equal_results_alone(precision):
         for a, b in zip(alone, mixed):
             assert np.array_equal(a, b), r.rid
     assert rep.p99_ms >= rep.p50_ms > 0 and rep.mlups > 0
+
+
+def test_served_results_match_the_oracle():
+    """Served FP64 results against the FP64 CPU oracle run of each request alone (1e-11 in
+    rho/u/T): Riemann tubes (outflow ends, tau = 1/2 with the sensor) and doubly periodic shear
+    layers, packed together and admitted while other requests run."""
+    from paper_1910_13515_gb300 import build
+    build.build()
+    from gpu_helpers import TOL, rel_diffs, run_oracle
+    from oracle import oracle39 as o
+    from paper_1910_13515_gb300.serve import GpuBackend, Scheduler
+
+    reqs = small_requests(8, seed=11)
+    kinds = {r.setup.name.split("_")[0] for r in reqs}
+    assert kinds == {"riemann", "shear"}
+    be = GpuBackend(precision=0, max_lattices=8, max_cells=1 << 16, graph_steps=8)
+    one = max(be.bytes_for(r.setup) for r in reqs)
+    rep = Scheduler(be, budget_bytes=3 * one, max_resident=4, chunk_steps=16).run(reqs)
+    be.close()
+    assert rep.max_resident >= 2
+    for r in reqs:
+        st, failed = run_oracle(r.setup, r.setup.steps)
+        assert failed == 0
+        d = rel_diffs(rep.results[r.rid], o.macros(st), r.setup.mask, r.setup.gamma)
+        assert max(d) <= TOL, (r.setup.name, d)

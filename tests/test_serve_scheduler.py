@@ -141,3 +141,67 @@ def test_no_withdrawal_changes_nothing():
                         sleep=clock.sleep).run(rs)
         runs.append((rep.results, rep.latencies_s, rep.rounds, rep.cancelled))
     assert runs[0] == runs[1] and runs[0][3] == {}
+
+
+class FakeAsyncBackend(FakeBackend):
+    """run() only enqueues: the run occupies the fake GPU until its end time; busy() reports
+    that, and steps are credited when the run ends.  Admissions while busy are recorded."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.end = 0.0
+        self.admitted_while_busy = 0
+        self.pending_run = None
+
+    def admit(self, setup):
+        if self.busy():
+            self.admitted_while_busy += 1
+        return super().admit(setup)
+
+    def run(self, n):
+        assert not self.busy()
+        self.pending_run = n
+        cells = sum(self.live[h].ncells * min(n, t - self.steps_done[h])
+                    for h, t in self.resident)
+        self.end = self.clock.t + cells * 1e-6 + 1e-6
+
+    def busy(self):
+        return self.clock.t < self.end
+
+    def wait(self):
+        if self.clock.t < self.end:
+            self.clock.t = self.end
+        if self.pending_run is not None:
+            n, self.pending_run = self.pending_run, None
+            for h, target in self.resident:
+                self.steps_done[h] += min(n, target - self.steps_done[h])
+
+    def set_resident(self, handles, steps):
+        assert not self.busy()
+        super().set_resident(handles, steps)
+
+    def read(self, h):
+        assert not self.busy()
+        return super().read(h)
+
+    def release(self, h):
+        assert not self.busy()
+        super().release(h)
+
+
+def test_arrivals_during_a_run_are_set_up_meanwhile_and_join_the_next_run():
+    """With an asynchronous backend the scheduler admits requests that arrive while a run is on
+    the GPU (their set-up overlaps it), never changes the resident set, reads or releases while
+    a run is in flight, and still gives every request exactly its steps within the budget."""
+    clock = FakeClock()
+    be = FakeAsyncBackend(clock)
+    reqs = make_requests(16, seed=3)
+    budget = 6 * 32 * 32 * 100
+    rep = Scheduler(be, budget, max_resident=6, chunk_steps=8, clock=clock,
+                    sleep=clock.sleep, poll_s=1e-4).run(reqs)
+    assert sorted(rep.results) == [r.rid for r in reqs]
+    for r in reqs:
+        assert rep.results[r.rid] == r.setup.steps
+    assert be.max_bytes_seen <= budget and not be.live
+    assert be.admitted_while_busy > 0
+    assert rep.cell_steps == sum(r.setup.ncells * r.setup.steps for r in reqs)
