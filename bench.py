@@ -679,6 +679,10 @@ def main():
                     help="arrival rate (Hz) of the serving section: saturating by default")
     ap.add_argument("--developed-at", type=int, default=3000,
                     help="airfoil section: first step of the developed-flow window")
+    ap.add_argument("--root-finder", default="newton", choices=["newton", "chord"],
+                    help="solver of the constraint equations (chord: the chord-Newton hybrid)")
+    ap.add_argument("--newton-tol", type=float, default=1e-12,
+                    help="stopping tolerance of the constraint solve (max |G_k| / rho)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -714,7 +718,9 @@ def main():
 
     prec = C.LBM39_FP64 if args.precision == "fp64" else C.LBM39_MIXED
     s = make_setup(args.workload, args.mach)
-    L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}")
+    solver = {"root_finder": 1 if args.root_finder == "chord" else 0,
+              "newton_tol": args.newton_tol}
+    L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}", **solver)
     stream = L.stream
     N = s.ncells
     st_init = L.stats()
@@ -745,21 +751,25 @@ def main():
     # lattices one cell thick in z with u_z = 0 take the nine-constraint (z-mirror) solve
     reduced = (args.precision == "fp64" and s.nz == 1 and not np.any(s.u[2])
                and s.u_inf[2] == 0.0)
-    model = FP64_FLOPS_MODEL["fp64_2d" if reduced else args.precision]
-    achieved_tf = (model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
+    model = FP64_FLOPS_MODEL.get(("fp64_2d" if reduced else args.precision)
+                                 + ("_chord" if args.root_finder == "chord" else ""))
+    achieved_tf = ((model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
+                   if model else None)
     hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["kernel_hash"] == kernel_source_hash() and args.mach == 0.8:
+    if (NCU_TRAFFIC["kernel_hash"] == kernel_source_hash() and args.mach == 0.8
+            and args.root_finder == "newton" and args.newton_tol == 1e-12):
         traffic = NCU_TRAFFIC["gb_per_launch"].get(f"{args.workload}/{args.precision}")
-    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4),
+    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4) if model else None,
                 "peak": round(peak_tf, 4), "unit": "TFLOP/s",
-                "frac": round(achieved_tf / peak_tf, 4),
+                "frac": round(achieved_tf / peak_tf, 4) if model else None,
                 "traffic": round(traffic * 1e9) if traffic else None,
                 "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
                                "(of measured)",
-                "flops_per_cell_update": round(model[0] + model[1] * k_upd),
-                "flops_model": f"{model[0]:g} + {model[1]:g} x (Newton updates per cell), fitted "
-                               "to ncu FP64 instruction counts (2 per DFMA, 1 per DADD/DMUL)",
+                "flops_per_cell_update": round(model[0] + model[1] * k_upd) if model else None,
+                "flops_model": (f"{model[0]:g} + {model[1]:g} x (Newton updates per cell), "
+                                "fitted to ncu FP64 instruction counts (2 per DFMA, 1 per "
+                                "DADD/DMUL)") if model else "none fitted for this solver",
                 "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": HBM_PEAK_GBS,
                         "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),
                         "bytes_per_update": BYTES_PER_UPDATE[args.precision],
@@ -820,7 +830,8 @@ def main():
 
     # the other parts of the metric, in the same line as the FP64 256^3 box
     sections = set() if args.sections == "none" else set(args.sections.split(","))
-    suite = (args.workload == "box256" and args.precision == "fp64" and world == 1)
+    suite = (args.workload == "box256" and args.precision == "fp64" and world == 1
+             and args.root_finder == "newton" and args.newton_tol == 1e-12)
     serving = airfoil = None
     if suite and "precision" in sections:
         form = precision_form_section(args, local, s, (headline_state, value))
@@ -839,6 +850,7 @@ def main():
 
     if rank == 0:
         config = {"workload": workload_text(args), "precision": args.precision,
+                  "root_finder": args.root_finder, "newton_tol": args.newton_tol,
                   "cells": N, "fluid_cells": int(fluid),
                   "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
                   "l2": "inputs larger than L2 (%.2f GB of populations)" % (

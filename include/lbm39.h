@@ -102,6 +102,18 @@ typedef struct {
                                Pr = (tau_eff - 1/2)/(tau2 - 1/2).  Mass, momentum and
                                energy are conserved as before.  Range [0.01, 100];
                                needs 2 C_v - D > 0 (gamma < 5/3). */
+  int32_t root_finder;      /* solver of the constraint equations in each time step
+                               (lbm39_init's cold start always uses Newton):
+                               0 (default): Newton-Raphson (Sec. 3);
+                               1: chord-Newton hybrid (the Sec. 6 outlook names other
+                               root finders): the same stopping rule, polishing step,
+                               budget and failure rule, but the direction reuses the
+                               LDL^T factor of the last Jacobian formed in the solve
+                               while the previous accepted step reduced max|G| by at
+                               least 1e-3 (a chord step), else forms J at the current
+                               point; a chord step that does not reduce ||G||_2 is
+                               replaced by a Newton step from the same point.  Converges
+                               to the same equilibrium; FP64 path with Pr = 1 only. */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;
@@ -120,7 +132,8 @@ typedef struct {
 
 /* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice
  * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 0,
- * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5), reduce_2d 1, Pr 1). */
+ * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5), reduce_2d 1, Pr 1,
+ * Newton root finder). */
 void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* The compiled D3Q39 velocity set (Sec. 3: (0,0,0), (1,0,0)_FS, (+-1,+-1,+-1),
@@ -240,8 +253,9 @@ int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precisio
 
 /* Makes lattices[0..n) the resident set; lattice j steps until its time
  * reaches t_end[j] (>= its current time).  Lattices must be initialised, of
- * the batch's precision, with Pr = 1 (lbm39_params.prandtl 1 or 0; other
- * lattices are rejected with LBM39_ERR_ARG), and stay alive while resident.
+ * the batch's precision, with Pr = 1 (lbm39_params.prandtl 1 or 0) and the
+ * Newton root finder (other lattices are rejected with LBM39_ERR_ARG), and
+ * stay alive while resident.
  * Synchronous. */
 int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_t* t_end,
                     int32_t n);

@@ -40,6 +40,7 @@ typedef struct {
   int32_t newton_min_upd; /* reading: at least this many updates per solve */
   double rho_inf, u_inf[3], T_inf; /* far-field state for freestream cells */
   double prandtl;      /* Prandtl number; 0 or 1: Pr = 1, plain BGK (Sec. 3) */
+  int32_t root_finder; /* 0: Newton-Raphson (Sec. 3); 1: chord-Newton hybrid (Sec. 6 outlook) */
 } o39_params;
 
 typedef struct {
@@ -335,6 +336,90 @@ int o39_newton(const double *m, double *lam, double tol, int maxit, int min_upd,
   return status;
 }
 
+/* Chord-Newton hybrid for the same 13 equations (the paper's outlook, Sec. 6,
+ * names other root finders; this one is the oracle's reading of a standard
+ * variant).  Same stopping rule, polishing step, budget and failure rule as
+ * o39_newton; the direction J^{-1} G reuses the last Jacobian formed in this
+ * solve (a chord step) as long as the previous accepted step reduced max|G|
+ * by at least the factor CHORD_RHO, and otherwise forms J at the current
+ * point (a Newton step).  A chord step that does not reduce ||G||_2 is not
+ * halved: J is formed at the current point instead and the update is retried
+ * as a Newton step.  Each Jacobian formed is counted in *n_jac_out.
+ * Near the root a chord step contracts the error by the relative change of J
+ * since it was formed, so after a Newton step of quadratic convergence the
+ * next steps can skip forming and inverting J. */
+#define CHORD_RHO 1e-3
+
+int o39_newton_hybrid(const double *m, double *lam, double tol, int maxit, int min_upd,
+                      int *n_upd_out, int *n_jac_out, double *F) {
+  build_lattice();
+  double G[NM], Ji[NM * NM];
+  o39_feq_norm(lam, F);
+  residual_from_F(F, m, G);
+  int n_upd = 0, n_jac = 0, status = 0, polished = 0, have_J = 0;
+  double r_prev = 0.0;  /* max|G| before the last accepted step; 0: none yet */
+  for (;;) {
+    double r = maxabs(G);
+    if (n_upd >= min_upd && r < tol && (r < 1e-2 * tol || polished)) break;
+    if (n_upd >= maxit) { status = 1; break; }
+    const int chord = have_J && r_prev > 0.0 && r <= CHORD_RHO * r_prev;
+    if (!chord) {
+      double J[NM * NM];
+      jacobian_from_F(F, J);
+      ++n_jac;
+      if (o39_invert(J, Ji) != 0) { status = 1; break; }
+      have_J = 1;
+    }
+    double d[NM];
+    for (int k = 0; k < NM; ++k) {
+      double s = 0.0;
+      for (int l = 0; l < NM; ++l) s += Ji[k * NM + l] * G[l];
+      d[k] = s;
+    }
+    double lt[NM], Ft[Q], Gt[NM];
+    polished = (r < tol);
+    if (polished) { /* polishing step: always full */
+      for (int k = 0; k < NM; ++k) lt[k] = lam[k] - d[k];
+      o39_feq_norm(lt, Ft);
+      residual_from_F(Ft, m, Gt);
+    } else {
+      double s0 = sumsq(G), t = 1.0;
+      int ok = 0;
+      for (int ls = 0; ls <= LS_MAX; ++ls) {
+        for (int k = 0; k < NM; ++k) lt[k] = lam[k] - t * d[k];
+        o39_feq_norm(lt, Ft);
+        residual_from_F(Ft, m, Gt);
+        if (sumsq(Gt) < s0) { ok = 1; break; }
+        if (chord) break; /* a chord step is not halved */
+        t *= 0.5;
+      }
+      if (!ok && chord) { /* retry from here with J formed at this point */
+        have_J = 0;
+        r_prev = 0.0;
+        polished = 0;
+        continue;
+      }
+      if (!ok) { status = 1; break; }
+    }
+    r_prev = r;
+    memcpy(lam, lt, sizeof lt);
+    memcpy(F, Ft, sizeof Ft);
+    memcpy(G, Gt, sizeof Gt);
+    ++n_upd;
+  }
+  if (n_upd_out) *n_upd_out = n_upd;
+  if (n_jac_out) *n_jac_out = n_jac;
+  return status;
+}
+
+/* The root finder the run parameters select. */
+static int solve13(const o39_params *p, const double *m, double *lam, int maxit, int *n_upd,
+                   double *F) {
+  if (p->root_finder == 1)
+    return o39_newton_hybrid(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, NULL, F);
+  return o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Fallback where the 13-moment equilibrium does not exist.
  * reading (the paper does not say what a cell does when its constraint solve
@@ -616,7 +701,7 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, uin
   const int flagged = *on_fb != 0;
   int maxit = p->newton_maxit;
   if (flagged) maxit = (t % RETRY_PERIOD == 0) ? RETRY_MAXIT : 0;
-  int st = o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
+  int st = solve13(p, m, lam, maxit, n_upd, F);
   if (st) {  /* counted as a failure: the cell takes the fallback this step */
     if (fallback_into(u, T, flagged ? lam_in : NULL, lam, F) == 0) {
       *on_fb = 1;

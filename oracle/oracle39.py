@@ -53,6 +53,7 @@ class Params(ctypes.Structure):
         ("u_inf", ctypes.c_double * 3),
         ("T_inf", ctypes.c_double),
         ("prandtl", ctypes.c_double),
+        ("root_finder", ctypes.c_int32),
     ]
 
 
@@ -87,6 +88,8 @@ def lib():
         _lib.o39_gaussian_guess.argtypes = [vp, d, vp]
         _lib.o39_newton.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib.o39_newton.restype = ctypes.c_int
+        _lib.o39_newton_hybrid.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        _lib.o39_newton_hybrid.restype = ctypes.c_int
         _lib.o39_alpha.argtypes = [d, d]
         _lib.o39_alpha.restype = d
         _lib.o39_cell_macros.argtypes = [P, vp, vp, vp, vp, vp]
@@ -188,6 +191,17 @@ def newton(m, lam0, tol=1e-12, maxit=30, min_upd=0):
     return lam, F, nu.value, st
 
 
+def newton_hybrid(m, lam0, tol=1e-12, maxit=30, min_upd=0):
+    """The chord-Newton hybrid: (lam, F, n_updates, n_jacobians, status)."""
+    lam = _f64(lam0).copy()
+    F = np.zeros(Q)
+    nu = ctypes.c_int(0)
+    nj = ctypes.c_int(0)
+    st = lib().o39_newton_hybrid(_p(_f64(m)), _p(lam), float(tol), int(maxit), int(min_upd),
+                                 ctypes.byref(nu), ctypes.byref(nj), _p(F))
+    return lam, F, nu.value, nj.value, st
+
+
 def targets5(u, T) -> np.ndarray:
     out = np.zeros(5)
     lib().o39_targets5(_p(_f64(u)), float(T), _p(out))
@@ -228,6 +242,7 @@ class Config:
     T_inf: float = 0.5
     init_maxit: int = 200
     prandtl: float = 1.0
+    root_finder: int = 0
 
     def params(self) -> Params:
         p = Params()
@@ -244,6 +259,7 @@ class Config:
         p.rho_inf = self.rho_inf
         p.T_inf = self.T_inf
         p.prandtl = self.prandtl
+        p.root_finder = int(self.root_finder)
         return p
 
     @property

@@ -204,13 +204,12 @@ __device__ __forceinline__ double sum_sq(const double (&v)[N]) {
   return s;
 }
 
-// In-place LDL^T of a packed symmetric N x N J (unit-lower L below a diagonal
-// D) and the solve J x = b (b overwritten by x).  False if a pivot is not
-// positive (J not numerically SPD).
+// In-place LDL^T of a packed symmetric N x N J: unit-lower L below a diagonal
+// D, with rd the reciprocals of D's entries.  False if a pivot is not positive
+// (J not numerically SPD).
 template <class T, int N = NM>
-__device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
+__device__ __forceinline__ bool ldlt_factor(T (&J)[N * (N + 1) / 2], T (&rd)[N]) {
   bool ok = true;
-  T rd[N];
   static_for<0, N>([&](auto JJ) {
     constexpr int j = decltype(JJ)::value;
     T v[N];
@@ -236,6 +235,13 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
       J[tri(i, j)] = a * rd[j];
     });
   });
+  return ok;
+}
+
+// Solve J x = b with the factor of ldlt_factor (b overwritten by x).
+template <class T, int N = NM>
+__device__ __forceinline__ void ldlt_apply(const T (&J)[N * (N + 1) / 2], const T (&rd)[N],
+                                           T (&b)[N]) {
   static_for<1, N>([&](auto II) {  // L y = b
     constexpr int i = decltype(II)::value;
     T a = b[i];
@@ -256,6 +262,15 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
     });
     b[i] = a;
   });
+}
+
+// In-place LDL^T of a packed symmetric N x N J and the solve J x = b (b
+// overwritten by x).  False if a pivot is not positive.
+template <class T, int N = NM>
+__device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
+  T rd[N];
+  const bool ok = ldlt_factor<T, N>(J, rd);
+  ldlt_apply<T, N>(J, rd, b);
   return ok;
 }
 
@@ -346,6 +361,88 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
     for (int k = 0; k < S::N; ++k) dl[k] = G[k];
     if (!newton_direction<BLK, MIXED, D2>(F, dl)) { failed = 1; break; }
     polished = r < ph.tol;
+    t = 1.0;
+    ls = 0;
+  }
+  return NewtonResult{n, failed};
+}
+
+// Chord-Newton hybrid for the same equations (a second root finder; the
+// paper's outlook names other root finders).  Same stopping rule, polishing
+// step, budget, line search and failure rule as newton(); the direction reuses
+// the LDL^T factor of the last Jacobian formed in this solve (a chord step)
+// while the previous accepted step reduced max|G| by at least CHORD_RHO, and
+// otherwise forms and factors J at the current point (a Newton step).  A chord
+// step that does not reduce ||G||_2 is not halved: the solve goes back to the
+// current point and takes a Newton step from there.  The factor (FP64) lives
+// across the evaluations of the solve.
+constexpr double CHORD_RHO = 1e-3;
+
+template <int BLK, bool D2 = false>
+__device__ NewtonResult newton_chord(WS<BLK> w, const Phys& ph, int maxit, bool cached) {
+  using S = Sys<D2>;
+  constexpr int N = S::N;
+  WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M), dl = w.at(WS_DL);
+  int n = 0, failed = 0, ls = 0;
+  bool first = true, polished = false, restore = false, refresh = false, chord = false;
+  bool have_J = false;
+  double t = 0.0, s0 = 0.0, r_prev = 0.0, r_dir = 0.0;
+  double Jf[N * (N + 1) / 2], rd[N];
+  for (;;) {
+    double G[N];
+    eval_equilibrium<BLK, D2>(lam, dl, t, F, m, G, first && cached);
+    if (restore) break;  // F is back at the last accepted lam after a failed line search
+    if (refresh) {
+      refresh = false;  // back at lam after a rejected chord step: a Newton step from here
+    } else {
+      if (!first && !polished && !(sum_sq(G) < s0)) {  // reject
+        if (chord) {  // a chord step is not halved
+          refresh = true;
+          have_J = false;
+          r_prev = 0.0;
+          t = 0.0;
+          continue;
+        }
+        if (++ls > LS_MAX) {
+          failed = 1;
+          restore = true;
+          t = 0.0;
+          continue;
+        }
+        t *= 0.5;
+        continue;
+      }
+      // accept the trial point
+      if (t != 0.0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) lam[S::idx(k)] = fma(-t, dl[k], lam[S::idx(k)]);
+      }
+      if (!first) {
+        ++n;
+        r_prev = r_dir;
+      }
+      first = false;
+    }
+    const double r = max_abs(G);
+    if (n >= ph.min_upd && r < ph.tol && (r < 1e-2 * ph.tol || polished)) break;
+    if (n >= maxit) { failed = 1; break; }
+    s0 = sum_sq(G);
+    chord = have_J && r_prev > 0.0 && r <= CHORD_RHO * r_prev;
+    if (!chord) {
+      double s[N];
+      if constexpr (D2) gen::moments2d<double>(F, s, Jf);
+      else gen::moments<double>(F, s, Jf);
+      if (!ldlt_factor<double, N>(Jf, rd)) { failed = 1; break; }
+      have_J = true;
+    }
+    double b[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) b[k] = G[k];
+    ldlt_apply<double, N>(Jf, rd, b);
+#pragma unroll
+    for (int k = 0; k < N; ++k) dl[k] = b[k];
+    polished = r < ph.tol;
+    r_dir = r;
     t = 1.0;
     ls = 0;
   }

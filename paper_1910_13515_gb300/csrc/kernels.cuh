@@ -427,7 +427,8 @@ __device__ __forceinline__ int retry_budget(long long t) {
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 // D2: the nine-function constraint system of a z-mirror-symmetric lattice one
 // cell thick in z (Sys<true>; the same values as the full system).
-template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false>
+// CHORD: the chord-Newton hybrid root finder (newton_chord; FP64 path only).
+template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false, bool CHORD = false>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
@@ -440,7 +441,9 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   // a marked cell off a retry step gets no update (it stays on the fallback
   // unless its embedding already meets the 13 constraints)
   const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
-  const NewtonResult nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
+  NewtonResult nr;
+  if constexpr (CHORD) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
+  else nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
@@ -452,7 +455,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
 }
 
 // One time step over every fluid cell (even or odd AA pass).
-template <bool ODD, class P, int BLK, bool D2, bool PR = false>
+template <bool ODD, class P, int BLK, bool D2, bool PR = false, bool CHORD = false>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
   if (cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID))
-    step_cell<ODD, P, BLK, D2, PR>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
+    step_cell<ODD, P, BLK, D2, PR, CHORD>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 

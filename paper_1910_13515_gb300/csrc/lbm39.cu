@@ -17,6 +17,7 @@
 #include "../../include/lbm39.h"
 #include "batch.cuh"
 #include "kernels.cuh"
+#include "chord.h"
 #include "lattice_view.h"
 #include "prandtl.h"
 
@@ -72,6 +73,11 @@ bool params_ok(const lbm39_params* p) {
   if (!(p->prandtl == 0.0 || p->prandtl == 1.0 ||
         (p->prandtl >= 0.01 && p->prandtl <= 100.0 && 2.0 / (p->gamma - 1.0) - D > 0.0)))
     return false;
+  // the chord-Newton hybrid serves the FP64 path with the paper's Pr = 1 collision
+  if (p->root_finder != 0 && p->root_finder != 1) return false;
+  if (p->root_finder == 1 &&
+      (p->precision != LBM39_FP64 || !(p->prandtl == 0.0 || p->prandtl == 1.0)))
+    return false;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? p->nx : a == 1 ? p->ny : p->nz;
     if (!p->periodic[a] && n < 7) return false;  // 3 boundary layers per end + fluid
@@ -108,6 +114,7 @@ uint64_t params_hash(const lbm39_params* p) {
   h = fnv1a(&p->T_inf, sizeof p->T_inf, h);
   h = fnv1a(&p->reduce_2d, sizeof p->reduce_2d, h);
   h = fnv1a(&p->prandtl, sizeof p->prandtl, h);
+  h = fnv1a(&p->root_finder, sizeof p->root_finder, h);
   return h;
 }
 
@@ -150,6 +157,14 @@ struct Launch {
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
     // the reduced (z-mirror) system serves the FP64 path only (see reduction_allowed)
     constexpr bool fp64 = sizeof(P) == 8;
+    if (fp64 && L->p.root_finder == 1) {  // chord-Newton hybrid root finder (chord.cu)
+      launch_step_chord(L->desc, odd, L->stream);
+      if (L->fills) {
+        if (odd) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+        else k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
+      }
+      return;
+    }
     if (L->desc.ph.pr_adjust) {  // Prandtl-number adjustment (prandtl.cu)
       launch_step_prandtl(L->desc, odd, !fp64, L->stream);
       if (L->fills) {
@@ -809,7 +824,8 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
     if (!L) return LBM39_ERR_ARG;
     if (!L->initialized) return LBM39_ERR_STATE;
     if (L->p.precision != B->precision || t_end[j] < L->t) return LBM39_ERR_ARG;
-    if (L->desc.ph.pr_adjust) return LBM39_ERR_ARG;  // the packed step is the Pr = 1 collision
+    // the packed step is the Pr = 1 collision with the Newton solver
+    if (L->desc.ph.pr_adjust || L->p.root_finder != 0) return LBM39_ERR_ARG;
     cells += L->N;
   }
   if (cells > B->maxcells) return LBM39_ERR_ARG;
@@ -1006,6 +1022,7 @@ bool lattice_view(const lbm39_lattice* L, LatticeView* v) {
   v->N = L->N;
   v->mixed = L->mixed;
   v->initialized = L->initialized;
+  v->chord = L->p.root_finder == 1;
   return true;
 }
 

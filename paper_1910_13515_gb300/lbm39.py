@@ -46,6 +46,7 @@ class lbm39_params(ctypes.Structure):
         ("rho_inf", ctypes.c_double), ("u_inf", ctypes.c_double * 3), ("T_inf", ctypes.c_double),
         ("reduce_2d", ctypes.c_int32),
         ("prandtl", ctypes.c_double),
+        ("root_finder", ctypes.c_int32),
     ]
 
 
