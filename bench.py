@@ -679,8 +679,11 @@ def main():
                     help="arrival rate (Hz) of the serving section: saturating by default")
     ap.add_argument("--developed-at", type=int, default=3000,
                     help="airfoil section: first step of the developed-flow window")
-    ap.add_argument("--root-finder", default="newton", choices=["newton", "chord"],
-                    help="solver of the constraint equations (chord: the chord-Newton hybrid)")
+    ap.add_argument("--root-finder", default="newton", choices=["newton", "chord", "fp32dir"],
+                    help="solver of the constraint equations (chord: the chord-Newton hybrid; "
+                         "fp32dir: Newton with a single-precision direction)")
+    ap.add_argument("--start-at", type=int, default=0,
+                    help="step the lattice to this time before the warm-up (developed flows)")
     ap.add_argument("--newton-tol", type=float, default=1e-12,
                     help="stopping tolerance of the constraint solve (max |G_k| / rho)")
     args = ap.parse_args()
@@ -718,13 +721,16 @@ def main():
 
     prec = C.LBM39_FP64 if args.precision == "fp64" else C.LBM39_MIXED
     s = make_setup(args.workload, args.mach)
-    solver = {"root_finder": 1 if args.root_finder == "chord" else 0,
+    solver = {"root_finder": {"newton": 0, "chord": 1, "fp32dir": 2}[args.root_finder],
               "newton_tol": args.newton_tol}
     L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}", **solver)
     stream = L.stream
     N = s.ncells
     st_init = L.stats()
     fluid = st_init.fluid_cells
+    while L.time < args.start_at:
+        L.step(min(500, args.start_at - L.time))
+        L.sync()
 
     L.step(args.warmup)
     L.sync()
@@ -752,7 +758,7 @@ def main():
     reduced = (args.precision == "fp64" and s.nz == 1 and not np.any(s.u[2])
                and s.u_inf[2] == 0.0)
     model = FP64_FLOPS_MODEL.get(("fp64_2d" if reduced else args.precision)
-                                 + ("_chord" if args.root_finder == "chord" else ""))
+                                 + ("" if args.root_finder == "newton" else "_" + args.root_finder))
     achieved_tf = ((model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
                    if model else None)
     hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
@@ -831,7 +837,8 @@ def main():
     # the other parts of the metric, in the same line as the FP64 256^3 box
     sections = set() if args.sections == "none" else set(args.sections.split(","))
     suite = (args.workload == "box256" and args.precision == "fp64" and world == 1
-             and args.root_finder == "newton" and args.newton_tol == 1e-12)
+             and args.root_finder == "newton" and args.newton_tol == 1e-12
+             and args.start_at == 0)
     serving = airfoil = None
     if suite and "precision" in sections:
         form = precision_form_section(args, local, s, (headline_state, value))
@@ -851,6 +858,7 @@ def main():
     if rank == 0:
         config = {"workload": workload_text(args), "precision": args.precision,
                   "root_finder": args.root_finder, "newton_tol": args.newton_tol,
+                  "timed_from_step": args.start_at + args.warmup,
                   "cells": N, "fluid_cells": int(fluid),
                   "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
                   "l2": "inputs larger than L2 (%.2f GB of populations)" % (

@@ -112,8 +112,15 @@ typedef struct {
                                while the previous accepted step reduced max|G| by at
                                least 1e-3 (a chord step), else forms J at the current
                                point; a chord step that does not reduce ||G||_2 is
-                               replaced by a Newton step from the same point.  Converges
-                               to the same equilibrium; FP64 path with Pr = 1 only. */
+                               replaced by a Newton step from the same point;
+                               2: Newton with a single-precision direction (the
+                               precision form's solver): the residual and the update
+                               in FP64, the Jacobian and its LDL^T in FP32, same
+                               stopping rule; each step contracts the residual by about
+                               cond(J) times the FP32 precision.
+                               1 and 2 converge to the same equilibrium as Newton (the
+                               residual that decides convergence is the FP64 one); FP64
+                               path with Pr = 1 only. */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;

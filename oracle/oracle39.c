@@ -40,7 +40,8 @@ typedef struct {
   int32_t newton_min_upd; /* reading: at least this many updates per solve */
   double rho_inf, u_inf[3], T_inf; /* far-field state for freestream cells */
   double prandtl;      /* Prandtl number; 0 or 1: Pr = 1, plain BGK (Sec. 3) */
-  int32_t root_finder; /* 0: Newton-Raphson (Sec. 3); 1: chord-Newton hybrid (Sec. 6 outlook) */
+  int32_t root_finder; /* 0: Newton-Raphson (Sec. 3); 1: chord-Newton hybrid; 2: Newton with a
+                          float direction (other root finders: Sec. 6 outlook) */
 } o39_params;
 
 typedef struct {
@@ -412,11 +413,110 @@ int o39_newton_hybrid(const double *m, double *lam, double tol, int maxit, int m
   return status;
 }
 
+/* Inverse of the n x n matrix Jin (n <= NM) in single precision: textbook
+ * Gauss-Jordan elimination with partial pivoting, every operation in float.
+ * Returns 0, or -1 if singular. */
+static int invert_float(const float *Jin, float *Jinv, int n) {
+  float a[NM][2 * NM];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      a[r][c] = Jin[r * n + c];
+      a[r][n + c] = (r == c) ? 1.0f : 0.0f;
+    }
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsf(a[r][c]) > fabsf(a[p][c])) p = r;
+    if (!(fabsf(a[p][c]) > 0.0f)) return -1;
+    if (p != c)
+      for (int k = 0; k < 2 * n; ++k) { float t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+    float piv = a[c][c];
+    for (int k = 0; k < 2 * n; ++k) a[c][k] /= piv;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      float fct = a[r][c];
+      if (fct == 0.0f) continue;
+      for (int k = 0; k < 2 * n; ++k) a[r][k] -= fct * a[c][k];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Jinv[r * n + c] = a[r][n + c];
+  return 0;
+}
+
+/* Newton with a single-precision direction (a third root finder; the
+ * paper's outlook names other root finders): the same stopping rule,
+ * polishing step, budget, line search and failure rule as o39_newton, with
+ * the residual G and the update of lam in double precision, but the
+ * direction d = J^{-1} G formed in float: F and G rounded to float, J summed
+ * and inverted in float.  An inexact Newton iteration (iterative refinement):
+ * each step contracts the residual by about cond(J) times the float
+ * precision instead of squaring it, and it converges to the same equilibrium,
+ * because the residual that decides convergence is the double-precision one. */
+int o39_newton_fp32dir(const double *m, double *lam, double tol, int maxit, int min_upd,
+                       int *n_upd_out, double *F) {
+  build_lattice();
+  double G[NM];
+  o39_feq_norm(lam, F);
+  residual_from_F(F, m, G);
+  int n_upd = 0, status = 0, polished = 0;
+  for (;;) {
+    double r = maxabs(G);
+    if (n_upd >= min_upd && r < tol && (r < 1e-2 * tol || polished)) break;
+    if (n_upd >= maxit) { status = 1; break; }
+    float J[NM * NM], Ji[NM * NM], Gf[NM];
+    for (int k = 0; k < NM; ++k)
+      for (int l = 0; l < NM; ++l) {
+        float s = 0.0f;
+        for (int i = 0; i < Q; ++i) {
+          double phi[NM];
+          basis_i(i, phi);
+          s += (float)F[i] * (float)phi[k] * (float)phi[l];
+        }
+        J[k * NM + l] = s;
+      }
+    if (invert_float(J, Ji, NM) != 0) { status = 1; break; }
+    for (int k = 0; k < NM; ++k) Gf[k] = (float)G[k];
+    double d[NM];
+    for (int k = 0; k < NM; ++k) {
+      float s = 0.0f;
+      for (int l = 0; l < NM; ++l) s += Ji[k * NM + l] * Gf[l];
+      d[k] = s;
+    }
+    double lt[NM], Ft[Q], Gt[NM];
+    polished = (r < tol);
+    if (polished) {
+      for (int k = 0; k < NM; ++k) lt[k] = lam[k] - d[k];
+      o39_feq_norm(lt, Ft);
+      residual_from_F(Ft, m, Gt);
+    } else {
+      double s0 = sumsq(G), t = 1.0;
+      int ok = 0;
+      for (int ls = 0; ls <= LS_MAX; ++ls) {
+        for (int k = 0; k < NM; ++k) lt[k] = lam[k] - t * d[k];
+        o39_feq_norm(lt, Ft);
+        residual_from_F(Ft, m, Gt);
+        if (sumsq(Gt) < s0) { ok = 1; break; }
+        t *= 0.5;
+      }
+      if (!ok) { status = 1; break; }
+    }
+    memcpy(lam, lt, sizeof lt);
+    memcpy(F, Ft, sizeof Ft);
+    memcpy(G, Gt, sizeof Gt);
+    ++n_upd;
+  }
+  if (n_upd_out) *n_upd_out = n_upd;
+  return status;
+}
+
 /* The root finder the run parameters select. */
 static int solve13(const o39_params *p, const double *m, double *lam, int maxit, int *n_upd,
                    double *F) {
   if (p->root_finder == 1)
     return o39_newton_hybrid(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, NULL, F);
+  if (p->root_finder == 2)
+    return o39_newton_fp32dir(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
   return o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
 }
 

@@ -90,6 +90,8 @@ def lib():
         _lib.o39_newton.restype = ctypes.c_int
         _lib.o39_newton_hybrid.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         _lib.o39_newton_hybrid.restype = ctypes.c_int
+        _lib.o39_newton_fp32dir.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp]
+        _lib.o39_newton_fp32dir.restype = ctypes.c_int
         _lib.o39_alpha.argtypes = [d, d]
         _lib.o39_alpha.restype = d
         _lib.o39_cell_macros.argtypes = [P, vp, vp, vp, vp, vp]
@@ -200,6 +202,16 @@ def newton_hybrid(m, lam0, tol=1e-12, maxit=30, min_upd=0):
     st = lib().o39_newton_hybrid(_p(_f64(m)), _p(lam), float(tol), int(maxit), int(min_upd),
                                  ctypes.byref(nu), ctypes.byref(nj), _p(F))
     return lam, F, nu.value, nj.value, st
+
+
+def newton_fp32dir(m, lam0, tol=1e-12, maxit=30, min_upd=0):
+    """Newton with a single-precision direction: (lam, F, n_updates, status)."""
+    lam = _f64(lam0).copy()
+    F = np.zeros(Q)
+    nu = ctypes.c_int(0)
+    st = lib().o39_newton_fp32dir(_p(_f64(m)), _p(lam), float(tol), int(maxit), int(min_upd),
+                                  ctypes.byref(nu), _p(F))
+    return lam, F, nu.value, st
 
 
 def targets5(u, T) -> np.ndarray:

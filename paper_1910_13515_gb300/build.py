@@ -1,8 +1,8 @@
 """Build the CUDA library liblbm39.so (sm_103a) in-tree with nvcc.
 
 Five translation units (lbm39.cu: the 13-moment model; diag.cu: its per-cell diagnostic
-fields; prandtl.cu: its step kernels with the Prandtl-number adjustment; chord.cu: its FP64 step
-kernels with the chord-Newton root finder; poly.cu: the polynomial comparison model), compiled in
+fields; prandtl.cu: its step kernels with the Prandtl-number adjustment; root_finders.cu: its FP64
+step kernels with the other root finders; poly.cu: the polynomial comparison model), compiled in
 parallel, then linked into one shared library.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler",
               "-fPIC", "-Xptxas", "-warn-spills"]
-SOURCES = ["lbm39.cu", "poly.cu", "diag.cu", "prandtl.cu", "chord.cu"]
+SOURCES = ["lbm39.cu", "poly.cu", "diag.cu", "prandtl.cu", "root_finders.cu"]
 
 
 def nvcc() -> str:

@@ -687,18 +687,17 @@ __device__ __forceinline__ bool screen_undecided(float s39, int emin, int emax, 
   return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;
 }
 
-// The same screen in the precision form, where the FP32 terms are |d_i| r_i with
-// d_i = f~_i - rf_i (stored deviation minus rf_i = f^eq_i - f_ref_i rounded to float)
-// and r_i = rcp32(rho~ F~_i).  With u = 2^-24: rf_i is within u|rf_i| of its FP64 value
-// and d_i within u|d_i| of f~_i - rf_i, so |d_i| is within u(|d_i| + |rf_i|) of
-// |f_i - f^eq_i|; r_i is within 7u of 1/f^eq_i (two float views 2u each, the product u,
-// rcp32 2u) and the product adds u; four interleaved partial sums of at most 10 terms
-// add at most 12u s.  In all |s32 - s| <= u (1.01 b + 22 s32) with b = sum_i |rf_i| r_i.
-// True when s32 or b is not finite (a view out of float's range makes r_i infinite), or
-// when s32 lies within 4u (b + 22 s32) (about twice the bound) of a threshold.
-__device__ __forceinline__ bool screen_undecided_dev(float s39, float b) {
-  if (!(s39 < 1e30f) || !(b < 1e30f)) return true;
-  const float band = 0x1p-22f * (b + 22.0f * s39);
+// The screen of the precision form, whose terms are |d_i| r_i with d_i = f~_i - rf_i
+// the float difference of the stored deviation and the equilibrium's, rf_i =
+// round_float(f^eq_i - f_ref_i), and r_i = rcp32(rho~ F~_i).  With u = 2^-24: d_i is
+// within u|d_i| of the exact difference, r_i within 7u of 1/f^eq_i (two float views 2u
+// each, the product u, rcp32 2u), the product adds u, and four interleaved partial sums
+// of at most 10 terms add at most 12u s: |s32 - s| <= 21u s32 to first order.  True when
+// s32 is not finite (a view out of float's range makes r_i infinite) or lies within
+// 2^-18 s32 (about twice the bound) of a threshold 39 * {1e-2, 1e-1, 1}.
+__device__ __forceinline__ bool screen_undecided_dev(float s39) {
+  if (!(s39 < 1e30f)) return true;
+  const float band = 0x1p-18f * s39;
   return fabsf(s39 - 0.39f) <= band || fabsf(s39 - 3.9f) <= band || fabsf(s39 - 39.0f) <= band;
 }
 

@@ -47,7 +47,7 @@ __device__ __forceinline__ Macro moments_at(const Desc& d, long long cell, bool 
 // equilibrium the next step relaxes to; n_upd: its Newton updates, -1 where
 // the solve fails (the cell takes the fallback equilibrium).  Non-fluid cells
 // read 0.  odd: the AA parity of the lattice's time.
-template <class P, bool D2, bool CHORD = false>
+template <class P, bool D2, int SOLVER = 0>
 __global__ void __launch_bounds__(BLK) k_diag_fields(Desc d, int odd, double* eps_out,
                                                      int* nupd_out) {
   extern __shared__ double smem[];
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(BLK) k_diag_fields(Desc d, int odd, double* ep
   const bool marked = is_fallback_embedding<BLK>(lam);
   const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
   NewtonResult nr;
-  if constexpr (CHORD) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
-  else nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
+  if constexpr (SOLVER == 1) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
+  else nr = newton<BLK, (sizeof(P) == 4) || SOLVER == 2, D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   double f[Q];
   if (odd) gather_f<true, P>(d, cell, f);
@@ -95,10 +95,14 @@ extern "C" int lbm39_diag_fields(lbm39_lattice* L, double* eps, int32_t* n_upd) 
   const int odd = (int)(v.desc.t & 1);
   if (v.mixed)
     k_diag_fields<float, false><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
-  else if (v.chord && v.desc.d2)
-    k_diag_fields<double, true, true><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
-  else if (v.chord)
-    k_diag_fields<double, false, true><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 1 && v.desc.d2)
+    k_diag_fields<double, true, 1><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 1)
+    k_diag_fields<double, false, 1><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 2 && v.desc.d2)
+    k_diag_fields<double, true, 2><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 2)
+    k_diag_fields<double, false, 2><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
   else if (v.desc.d2)
     k_diag_fields<double, true><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
   else

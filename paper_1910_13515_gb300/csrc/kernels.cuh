@@ -279,31 +279,31 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
   } else {
     // precision form: h~ = h - h_ref stored in FP32; equilibrium deviation
     // h^eq - h_ref formed in FP64 and rounded; sensor and BGK in FP32.
-    // FP32 screen of s = 39 eps with its own error scale (screen_undecided_dev); the FP64
-    // value of the stored state where the screen cannot decide the branch of Eq. (alpha)
+    // The sensor compares each stored deviation with the equilibrium in the same storage,
+    // rf_i = (f^eq_i - f_ref_i) rounded to float: s = 39 eps = sum_i |f~_i - rf_i| / f^eq_i.
+    // FP32 screen, and the FP64 value of the same sum where the screen cannot decide the
+    // branch of Eq. (alpha) (screen_undecided_dev), so alpha is an FP64 decision.
     const double* __restrict__ href = d.href;
     P f[Q];
     gather<ODD, P>(d, cell, nb, 0, f);
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ref[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double Fi = F[i];
-      const float rf = round_float(fma(rho, Fi, -__ldg(href + i)));  // f^eq - f_ref
-      f[i] -= rf;                                                     // f - f^eq
-      const float r = rcp32(rho32 * trunc_float(Fi));
-      acc[i & 3] += fabsf(f[i]) * r;
-      ref[i & 3] += fabsf(rf) * r;
+      f[i] -= round_float(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
+      acc[i & 3] += fabsf(f[i]) * rcp32(rho32 * trunc_float(Fi));
     }
     const float s32 = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     eps = (double)s32 * (1.0 / Q);
-    if (screen_undecided_dev(s32, (ref[0] + ref[1]) + (ref[2] + ref[3]))) {
+    if (screen_undecided_dev(s32)) {
       P fs[Q];
       gather<ODD, P>(d, cell, nb, 0, fs);  // the stored values (cached)
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const double feq = rho * F[i];
-        s += fabs((exact_double(fs[i]) + __ldg(href + i)) - feq) / feq;
+        const float rf = round_float(fma(rho, F[i], -__ldg(href + i)));
+        s += fabs(exact_double(fs[i]) - exact_double(rf)) / feq;  // the difference is exact
       }
       eps = s * (1.0 / Q);
     }
@@ -427,8 +427,11 @@ __device__ __forceinline__ int retry_budget(long long t) {
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 // D2: the nine-function constraint system of a z-mirror-symmetric lattice one
 // cell thick in z (Sys<true>; the same values as the full system).
-// CHORD: the chord-Newton hybrid root finder (newton_chord; FP64 path only).
-template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false, bool CHORD = false>
+// SOLVER: the root finder of the constraint equations (FP64 path; the precision
+// form always uses 0): 0 Newton-Raphson; 1 the chord-Newton hybrid (newton_chord);
+// 2 Newton with a single-precision direction (newton<BLK, true>, the precision
+// form's solver).
+template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false, int SOLVER = 0>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
   WS<BLK> F = w.at(WS_E), lam = w.at(WS_LAM), m = w.at(WS_M);
@@ -442,8 +445,8 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   // unless its embedding already meets the 13 constraints)
   const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
   NewtonResult nr;
-  if constexpr (CHORD) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
-  else nr = newton<BLK, (sizeof(P) == 4), D2>(w, d.ph, maxit, true);
+  if constexpr (SOLVER == 1) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
+  else nr = newton<BLK, (sizeof(P) == 4) || SOLVER == 2, D2>(w, d.ph, maxit, true);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
@@ -455,7 +458,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
 }
 
 // One time step over every fluid cell (even or odd AA pass).
-template <bool ODD, class P, int BLK, bool D2, bool PR = false, bool CHORD = false>
+template <bool ODD, class P, int BLK, bool D2, bool PR = false, int SOLVER = 0>
 __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   extern __shared__ double smem[];
   __shared__ unsigned int s_ctr[CTR_N];
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
   load_exp_table();
   const long long cell = (long long)blockIdx.x * BLK + threadIdx.x;
   if (cell < d.N && (d.mask == nullptr || d.mask[cell] == MASK_FLUID))
-    step_cell<ODD, P, BLK, D2, PR, CHORD>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
+    step_cell<ODD, P, BLK, D2, PR, SOLVER>(d, cell, WS<BLK>{smem + threadIdx.x}, s_ctr);
   flush_stats<BLK>(s_ctr, d.ctr);
 }
 

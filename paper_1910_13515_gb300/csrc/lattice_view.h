@@ -15,7 +15,7 @@ struct LatticeView {
   long long N;          // cells
   bool mixed;           // precision form (FP32 deviation storage)
   bool initialized;     // lbm39_init has run
-  bool chord;           // the chord-Newton hybrid root finder (FP64)
+  int solver;           // root finder of the FP64 path (lbm39_params.root_finder)
 };
 
 // False for a NULL lattice or view.

@@ -17,9 +17,9 @@
 #include "../../include/lbm39.h"
 #include "batch.cuh"
 #include "kernels.cuh"
-#include "chord.h"
 #include "lattice_view.h"
 #include "prandtl.h"
+#include "root_finders.h"
 
 using namespace lbm39;
 
@@ -73,9 +73,9 @@ bool params_ok(const lbm39_params* p) {
   if (!(p->prandtl == 0.0 || p->prandtl == 1.0 ||
         (p->prandtl >= 0.01 && p->prandtl <= 100.0 && 2.0 / (p->gamma - 1.0) - D > 0.0)))
     return false;
-  // the chord-Newton hybrid serves the FP64 path with the paper's Pr = 1 collision
-  if (p->root_finder != 0 && p->root_finder != 1) return false;
-  if (p->root_finder == 1 &&
+  // the other root finders serve the FP64 path with the paper's Pr = 1 collision
+  if (p->root_finder < 0 || p->root_finder > 2) return false;
+  if (p->root_finder != 0 &&
       (p->precision != LBM39_FP64 || !(p->prandtl == 0.0 || p->prandtl == 1.0)))
     return false;
   for (int a = 0; a < 3; ++a) {
@@ -157,8 +157,8 @@ struct Launch {
     const unsigned fgrid = (unsigned)((L->N + 255) / 256);
     // the reduced (z-mirror) system serves the FP64 path only (see reduction_allowed)
     constexpr bool fp64 = sizeof(P) == 8;
-    if (fp64 && L->p.root_finder == 1) {  // chord-Newton hybrid root finder (chord.cu)
-      launch_step_chord(L->desc, odd, L->stream);
+    if (fp64 && L->p.root_finder != 0) {  // other root finders (root_finders.cu)
+      launch_step_root_finder(L->desc, odd, L->p.root_finder, L->stream);
       if (L->fills) {
         if (odd) k_fill_odd<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
         else k_fill_even<P><<<fgrid, 256, 0, L->stream>>>(L->desc);
@@ -1022,7 +1022,7 @@ bool lattice_view(const lbm39_lattice* L, LatticeView* v) {
   v->N = L->N;
   v->mixed = L->mixed;
   v->initialized = L->initialized;
-  v->chord = L->p.root_finder == 1;
+  v->solver = L->p.precision == LBM39_FP64 ? L->p.root_finder : 0;
   return true;
 }
 

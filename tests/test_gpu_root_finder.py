@@ -1,8 +1,8 @@
-"""The chord-Newton hybrid root finder (lbm39_params.root_finder = 1) on the GPU against the
-oracle's hybrid (oracle39.c o39_newton_hybrid), through the C ABI: FP64 parity to 1e-11 in
-rho/u/T on the full 13-constraint solve and the z-mirror reduced one, the same Newton-update
-counts, and the same flow as the Newton root finder (both solve every cell below the same
-residual)."""
+"""The other root finders of the constraint equations on the GPU against the oracle's
+(lbm39_params.root_finder 1: the chord-Newton hybrid, oracle39.c o39_newton_hybrid; 2: Newton with
+a single-precision direction, o39_newton_fp32dir), through the C ABI: FP64 parity to 1e-11 in
+rho/u/T on the full 13-constraint solve and the z-mirror reduced one, the Newton-update counts,
+and the same flow as the Newton root finder (all solve every cell below the same residual)."""
 import numpy as np
 import pytest
 
@@ -30,30 +30,34 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("solver", [1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_chord_newton_parity(mods, case):
+def test_root_finder_parity(mods, case, solver):
     C, Lattice = mods
     make, n = CASES[case]
     s = make()
-    L = Lattice.from_setup(s, root_finder=1)
+    L = Lattice.from_setup(s, root_finder=solver)
     L.step(n)
     assert L.sync() == 0
-    st, fo = run_oracle(s, n, root_finder=1)
+    st, fo = run_oracle(s, n, root_finder=solver)
     assert fo == 0
     d = rel_diffs(L.read_numpy(), o.macros(st), s.mask, s.gamma)
     assert max(d) <= TOL, d
     gs = L.stats()
-    assert abs(gs.newton_updates - st.stats.newton_updates) <= 1e-3 * st.stats.newton_updates + 2
+    # solver 2 forms its direction in FP32 with another summation and factorisation than the
+    # oracle's, so a few cells may take one update more or less
+    slack = 1e-3 if solver == 1 else 2e-2
+    assert abs(gs.newton_updates - st.stats.newton_updates) <= slack * st.stats.newton_updates + 2
     # the same equilibria as Newton-Raphson: the Newton oracle run agrees too
     st0, _ = run_oracle(s, n)
     assert max(rel_diffs(L.read_numpy(), o.macros(st0), s.mask, s.gamma)) <= TOL
 
 
-def test_chord_newton_only_for_fp64_pr1(mods):
+def test_other_root_finders_only_for_fp64_pr1(mods):
     C, Lattice = mods
     from paper_1910_13515_gb300.lattice import params_from_setup
     s = inputs.box(seed=2, shape=(4, 4, 4))
     for over in ({"root_finder": 1, "precision": 1}, {"root_finder": 1, "prandtl": 0.71},
-                 {"root_finder": 2}):
+                 {"root_finder": 2, "precision": 1}, {"root_finder": 3}, {"root_finder": -1}):
         rc, _, _ = C.lbm39_query_bytes(params_from_setup(s, **over))
         assert rc == C.LBM39_ERR_ARG, over

@@ -100,3 +100,38 @@ def test_lattice_run_with_the_hybrid_matches_newton(oracle):
     for x, y in zip(a[:3], b[:3]):
         assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
     assert nb >= na  # the hybrid takes more (cheaper) updates
+
+
+def test_fp32_direction_reaches_the_same_equilibrium(oracle):
+    """Newton with a single-precision direction (root_finder 2): the residual that decides
+    convergence is the double-precision one, so it lands on the Maxwell-Boltzmann moments to
+    1e-12 and on Newton's equilibrium, from cold and warm starts."""
+    vel, _, _ = oracle.lattice()
+    extra = 0
+    for _ in range(200):
+        u, T = random_state(RNG)
+        m = mb_targets(u, T)
+        lam, F, n, st = oracle.newton_fp32dir(m, oracle.gaussian_guess(u, T), maxit=200)
+        assert st == 0
+        assert np.all(np.abs(moments(vel, F) - m) <= 1e-12 * np.maximum(1, np.abs(m)))
+        lam0 = lam
+        m2 = mb_targets(u + RNG.normal(scale=0.02, size=3), T + RNG.normal(scale=0.01))
+        l1, F1, k1, s1 = oracle.newton(m2, lam0)
+        l2, F2, k2, s2 = oracle.newton_fp32dir(m2, lam0)
+        assert s1 == 0 and s2 == 0
+        assert np.abs(F1 - F2).max() <= 1e-12 * F1.max()
+        extra += k2 - k1
+    assert extra >= 0  # a linear rate: never fewer updates than Newton in total
+
+
+def test_lattice_run_with_the_fp32_direction_matches_newton(oracle):
+    s = inputs.box(seed=3, shape=(10, 10, 10))
+    runs = []
+    for rf in (0, 2):
+        cfg = oracle.Config(nx=s.nx, ny=s.ny, nz=s.nz, gamma=s.gamma, tau=s.tau,
+                            kn_sensor=s.kn_sensor, root_finder=rf)
+        st = oracle.init(cfg, s.mask, s.rho, s.u, s.T)
+        assert oracle.step(st, 20) == 0
+        runs.append(oracle.macros(st))
+    for x, y in zip(runs[0][:3], runs[1][:3]):
+        assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
