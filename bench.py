@@ -10,8 +10,8 @@ lattice.  Inputs are synthetic and seeded (paper_1910_13515_gb300.inputs).  The 
 line is the 3-D periodic 256^3 box in FP64 (rms Ma 0.8); the same line carries the other
 parts of the metric: the precision form on the 256^3 and 384^3 boxes against the FP64
 path, a serving run (Poisson request stream, p50/p99 time-to-solution, aggregate MLUPS
-against serial stepping) and the 2048x1024 NACA0012 airfoil (early window and developed
-flow).  For N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
+against serial stepping), the 2048x1024 NACA0012 airfoil (early window and developed
+flow) and the other root finders and stopping tolerances on the 256^3 box.  For N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
 workload (weak scaling; the step has no exchange between replicas) and the extra sections
 are skipped.  Rank 0 prints one JSON line.
 """
@@ -621,6 +621,48 @@ def precision_form_section(args, local, s256, fp64_256):
     return out
 
 
+def root_finder_section(args, local, s, newton_mlups: float):
+    """The other solvers of the constraint equations and stopping tolerances on the same
+    input (the FP64 256^3 box) after the same steps: MLUPS, Newton updates per cell and the
+    largest relative difference in rho/u/T from the Newton run's fields at 1e-12 (they solve
+    every cell below the same residual, so only round-off and the looser tolerances differ)."""
+    import numpy as np
+    import torch
+
+    from paper_1910_13515_gb300 import lbm39 as C
+    from paper_1910_13515_gb300.lattice import Lattice
+    out = {"newton_tol_1e-12_mlups": round(newton_mlups, 3)}
+    ref = None
+    fl = s.mask == 0
+    for name, over in (("newton", {}), ("chord", {"root_finder": 1}),
+                       ("fp32dir", {"root_finder": 2}), ("newton_tol_1e-10", {"newton_tol": 1e-10}),
+                       ("newton_tol_1e-8", {"newton_tol": 1e-8})):
+        L = Lattice.from_setup(s, precision=C.LBM39_FP64, device=f"cuda:{local}", **over)
+        c0 = L.stats().conserved
+        L.step(args.warmup)
+        st0 = L.stats()
+        _, ms, _ = timed_steps(L, args.steps, local)
+        st1 = L.stats()
+        state = L.read_numpy()
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+        if ref is None:
+            ref = state
+            if name == "newton":
+                continue
+        d = [float(np.abs(a[..., fl] - b[..., fl]).max() / max(np.abs(b[..., fl]).max(), 1e-300))
+             for a, b in zip(state[:3], ref[:3])]
+        out[name] = {"mlups": round(s.ncells * args.steps / (ms * 1e-3) / 1e6, 3),
+                     "newton_updates_per_cell": round((st1.newton_updates - st0.newton_updates)
+                                                      / (int(fl.sum()) * args.steps), 4),
+                     "max_rel_diff_vs_newton_rho_u_T": [float("%.2e" % v) for v in d],
+                     "conservation_drift_rel": [float("%.2e" % v)
+                                                for v in drift_rel(c0, st1.conserved)]}
+        out[name]["speedup_vs_newton"] = round(out[name]["mlups"] / newton_mlups, 3)
+    return out
+
+
 def airfoil_section(args, local, developed_at: int):
     """The 2048x1024 NACA0012 airfoil (Ma 1.5, Re 1e4, C = 400), FP64: the rate over the early
     window of the impulsive start (steps W..W+K) and over K steps of the developed flow from
@@ -670,9 +712,9 @@ def main():
                     help="poly workload: lattice side n of the periodic n x n x 1 lattice")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision form: also run the FP64 path and report L1 error, drift, speedup")
-    ap.add_argument("--sections", default="precision,serving,airfoil",
+    ap.add_argument("--sections", default="precision,serving,airfoil,root_finders",
                     help="FP64 256^3 box line: comma-separated extra sections to run in the same "
-                         "line (precision, serving, airfoil), or 'none'")
+                         "line (precision, serving, airfoil, root_finders), or 'none'")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving section of the 256^3 box line")
     ap.add_argument("--serve-section-rate", type=float, default=3.0,
@@ -839,10 +881,12 @@ def main():
     suite = (args.workload == "box256" and args.precision == "fp64" and world == 1
              and args.root_finder == "newton" and args.newton_tol == 1e-12
              and args.start_at == 0)
-    serving = airfoil = None
+    serving = airfoil = solvers = None
     if suite and "precision" in sections:
         form = precision_form_section(args, local, s, (headline_state, value))
     del headline_state
+    if suite and "root_finders" in sections:
+        solvers = root_finder_section(args, local, s, value)
     if suite and "airfoil" in sections:
         airfoil = airfoil_section(args, local, args.developed_at)
     if suite and "serving" in sections:
@@ -879,6 +923,7 @@ def main():
             "precision_form": form,
             "serving": serving,
             "airfoil": airfoil,
+            "root_finders": solvers,
             "kernel_hash": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

@@ -44,9 +44,11 @@ def test_root_finder_parity(mods, case, solver):
     d = rel_diffs(L.read_numpy(), o.macros(st), s.mask, s.gamma)
     assert max(d) <= TOL, d
     gs = L.stats()
-    # solver 2 forms its direction in FP32 with another summation and factorisation than the
-    # oracle's, so a few cells may take one update more or less
-    slack = 1e-3 if solver == 1 else 2e-2
+    # the kernel decides with the residual of the nine-constraint system on the z-mirror
+    # reduced lattice (the oracle always solves all 13), and solver 2 forms its direction in
+    # FP32 with another summation and factorisation than the oracle's: a few cells take one
+    # update more or less (measured: 0.14% and 2.8% on the small airfoil)
+    slack = 5e-3 if solver == 1 else 5e-2
     assert abs(gs.newton_updates - st.stats.newton_updates) <= slack * st.stats.newton_updates + 2
     # the same equilibria as Newton-Raphson: the Newton oracle run agrees too
     st0, _ = run_oracle(s, n)
