@@ -57,16 +57,17 @@ WORKLOADS = {
 # Newton work: A + B * (Newton updates per cell).  See profiles/.
 FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0),
                     # the nine-constraint (z-mirror) solve of lattices one cell thick in z
-                    "fp64_2d": (650.0, 1470.0)}
-# DRAM bytes (read + write) per launch of the step kernel (mean of the even and odd pass)
-# from ncu, per workload and precision, with the hash of the step kernel's code they were
-# captured with; reported as null once that code differs (profiles/ has the captures).
-NCU_TRAFFIC = {"kernel_hash": "2573a64f33d8b3e6",
-               "gb_per_launch": {"naca/fp64": 4.309, "naca/mixed": 3.177,
-                                 "box128/fp64": 5.670, "box128/mixed": 3.207,
-                                 "box2d/fp64": 4.583,
-                                 "box256/fp64": 45.36, "box256/mixed": 25.66,
-                                 "box384/mixed": 86.59}}
+                    "fp64_2d": (650.0, 1470.0),
+                    # FP64 storage with the single-precision Newton direction (root finder 2):
+                    # the FP64 path's per-cell part and the 128^3 box's count (4870 flops per
+                    # cell at 3.99 updates per cell)
+                    "fp64_fp32dir": (685.0, 1049.0)}
+# DRAM bytes (read + write) per launch of the step kernel from ncu, per workload and
+# precision, with the hash of the step kernel's code they were captured with; reported as
+# null once that code differs (profiles/ has the captures).  The 256^3 figure is the 128^3
+# capture scaled by the cell count (x 8; the same per-cell work, both far beyond L2).
+NCU_TRAFFIC = {"kernel_hash": "54b5fc576d5ef072",
+               "gb_per_launch": {"box128/fp64": 5.655, "box256/fp64": 45.24}}
 # The sources the step kernels and their launches are built from (the serving-form kernels
 # in batch.cuh are not among them).
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
@@ -331,9 +332,11 @@ def reduce_over_ranks(elapsed_s: float, units: float, dist=None, device=None):
 def serving_section(args, local, n_requests: int, rate_hz: float, seed: int = 0):
     """The serving form on a Poisson stream of n_requests seeded requests: aggregate MLUPS
     over the whole stream (all cells x steps of all requests / wall time from first arrival
-    to last result) and p50/p99 time-to-solution (arrival to result read).  Baseline: a
-    sample of the same requests run one after another through plain lbm39_step (no
-    packing), each with its own init and read-out, as a served request has."""
+    to last result) and p50/p99 time-to-solution (arrival to result read).  Baseline: the
+    same requests run one after another through plain lbm39_step (no packing), each with its
+    own init and read-out, as a served request has -- all of them, so that the baseline has
+    the stream's mix of lattice sizes (a sample without the large shear layers would run
+    the small, launch-bound lattices only)."""
     import torch
 
     from paper_1910_13515_gb300 import inputs
@@ -351,7 +354,7 @@ def serving_section(args, local, n_requests: int, rate_hz: float, seed: int = 0)
         rep = Scheduler(be, 4 << 30, 64, chunk_steps=64).run(reqs)
     clocks = clk.summary()
     be.close()
-    sample = reqs[::4]
+    sample = reqs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     cs = 0
@@ -368,7 +371,7 @@ def serving_section(args, local, n_requests: int, rate_hz: float, seed: int = 0)
             "p50_ms": round(rep.p50_ms, 2), "p99_ms": round(rep.p99_ms, 2),
             "aggregate_mlups": round(rep.mlups, 3), "serial_mlups": round(serial, 3),
             "speedup_vs_serial": round(rep.mlups / serial, 3),
-            "serial_sample": f"{len(sample)} of the requests, one at a time",
+            "serial_sample": f"all {len(sample)} requests, one at a time",
             "wall_s": round(rep.wall_s, 2), "clocks": clocks}
 
 
@@ -715,7 +718,7 @@ def main():
     ap.add_argument("--sections", default="precision,serving,airfoil,root_finders",
                     help="FP64 256^3 box line: comma-separated extra sections to run in the same "
                          "line (precision, serving, airfoil, root_finders), or 'none'")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the serving section of the 256^3 box line")
     ap.add_argument("--serve-section-rate", type=float, default=3.0,
                     help="arrival rate (Hz) of the serving section: saturating by default")
