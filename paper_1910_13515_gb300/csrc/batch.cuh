@@ -21,7 +21,10 @@ struct Tile {
   long long cell0;  // first cell of the tile
 };
 
-template <class P, int BLK>
+// D2: every lattice of these tiles takes the nine-constraint (z-mirror) solve
+// (FP64 lattices one cell thick in z with u_z = 0); the host sorts the tiles by
+// constraint system and launches one instantiation for each.
+template <class P, int BLK, bool D2>
 __global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict__ E,
                                                     const Tile* __restrict__ tiles, int s) {
   extern __shared__ double smem[];
@@ -41,14 +44,8 @@ __global__ void __launch_bounds__(BLK) k_batch_step(const BatchEntry* __restrict
   const long long cell = tl.cell0 + threadIdx.x;
   if (cell < sd.N && (sd.mask == nullptr || sd.mask[cell] == MASK_FLUID)) {
     WS<BLK> w{smem + threadIdx.x};
-    // the lattice's constraint system (the z-mirror reduction serves FP64 lattices only)
-    if (sizeof(P) == 8 && sd.d2) {
-      if (t & 1) step_cell<true, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
-      else step_cell<false, P, BLK, sizeof(P) == 8>(sd, cell, w, s_ctr);
-    } else {
-      if (t & 1) step_cell<true, P, BLK>(sd, cell, w, s_ctr);
-      else step_cell<false, P, BLK>(sd, cell, w, s_ctr);
-    }
+    if (t & 1) step_cell<true, P, BLK, D2>(sd, cell, w, s_ctr);
+    else step_cell<false, P, BLK, D2>(sd, cell, w, s_ctr);
   }
   flush_stats<BLK>(s_ctr, sd.ctr);
 }

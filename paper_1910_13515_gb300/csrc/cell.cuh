@@ -206,35 +206,62 @@ __device__ __forceinline__ double sum_sq(const double (&v)[N]) {
 
 // In-place LDL^T of a packed symmetric N x N J: unit-lower L below a diagonal
 // D, with rd the reciprocals of D's entries.  False if a pivot is not positive
-// (J not numerically SPD).
+// (J not numerically SPD).  FP64: right-looking elimination -- pivot k scales
+// its column once (L_ik = a_ik / d_k) and updates the trailing matrix with
+// a_ij -= L_ik a_jk, so each multiplier is one product and every other
+// operation a fused multiply-add (the FP64 pipe bounds the step).  FP32 (the
+// precision form's direction): left-looking, with v_k = L_jk d_k formed per
+// column, which keeps fewer values live.
 template <class T, int N = NM>
 __device__ __forceinline__ bool ldlt_factor(T (&J)[N * (N + 1) / 2], T (&rd)[N]) {
   bool ok = true;
-  static_for<0, N>([&](auto JJ) {
-    constexpr int j = decltype(JJ)::value;
-    T v[N];
-    static_for<0, j>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      v[k] = J[tri(j, k)] * J[tri(k, k)];
+  if constexpr (sizeof(T) == 8) {
+    static_for<0, N>([&](auto KK) {
+      constexpr int k = decltype(KK)::value;
+      const T dk = J[tri(k, k)];
+      ok = ok && (dk > T(0));
+      rd[k] = recip(dk);
+      T w[N];  // column k below the pivot, unscaled
+      static_for<k + 1, N>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        w[i] = J[tri(i, k)];
+        J[tri(i, k)] = w[i] * rd[k];
+      });
+      static_for<k + 1, N>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        static_for<k + 1, i + 1>([&](auto JJ) {
+          constexpr int j = decltype(JJ)::value;
+          J[tri(i, j)] = fma(-J[tri(i, k)], w[j], J[tri(i, j)]);
+        });
+      });
     });
-    T dj = J[tri(j, j)];
-    static_for<0, j>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      dj = fma(-J[tri(j, k)], v[k], dj);
-    });
-    ok = ok && (dj > T(0));
-    J[tri(j, j)] = dj;
-    rd[j] = recip(dj);
-    static_for<j + 1, N>([&](auto II) {
-      constexpr int i = decltype(II)::value;
-      T a = J[tri(i, j)];
+  } else {
+    static_for<0, N>([&](auto JJ) {
+      constexpr int j = decltype(JJ)::value;
+      T v[N];
       static_for<0, j>([&](auto K) {
         constexpr int k = decltype(K)::value;
-        a = fma(-J[tri(i, k)], v[k], a);
+        v[k] = J[tri(j, k)] * J[tri(k, k)];
       });
-      J[tri(i, j)] = a * rd[j];
+      T dj = J[tri(j, j)];
+      static_for<0, j>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        dj = fma(-J[tri(j, k)], v[k], dj);
+      });
+      ok = ok && (dj > T(0));
+      J[tri(j, j)] = dj;
+      rd[j] = recip(dj);
+      static_for<j + 1, N>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        T a = J[tri(i, j)];
+        static_for<0, j>([&](auto K) {
+          constexpr int k = decltype(K)::value;
+          a = fma(-J[tri(i, k)], v[k], a);
+        });
+        J[tri(i, j)] = a * rd[j];
+      });
     });
-  });
+  }
   return ok;
 }
 
@@ -282,12 +309,13 @@ template <int BLK, bool MIXED, bool D2 = false>
 __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
   constexpr int N = Sys<D2>::N;
   if constexpr (!MIXED) {
-    double J[N * (N + 1) / 2], s[N], b[N];
+    double J[N * (N + 1) / 2], s[N], b[N], rd[N];
     if constexpr (D2) gen::moments2d<double>(F, s, J);
     else gen::moments<double>(F, s, J);
+    const bool ok = ldlt_factor<double, N>(J, rd);
 #pragma unroll
-    for (int k = 0; k < N; ++k) b[k] = dl[k];
-    const bool ok = ldlt_solve<double, N>(J, b);
+    for (int k = 0; k < N; ++k) b[k] = dl[k];  // the right-hand side, once J is factored
+    ldlt_apply<double, N>(J, rd, b);
 #pragma unroll
     for (int k = 0; k < N; ++k) dl[k] = b[k];
     return ok;

@@ -730,6 +730,7 @@ struct lbm39_batch {
   Tile* dF = nullptr;
   std::vector<BatchEntry> hE;
   std::vector<Tile> hT, hF;
+  int nT2 = 0;  // leading tiles of hT whose lattices take the nine-constraint (z-mirror) solve
   std::vector<lbm39_lattice*> lats;
   std::vector<long long> tend;
   cudaGraphExec_t exec = nullptr;
@@ -756,8 +757,12 @@ BatchLayout batch_layout(int maxlat, long long maxcells) {
 
 template <class P>
 int batch_enqueue(lbm39_batch* B, int s) {
-  const int nt = (int)B->hT.size(), nf = (int)B->hF.size();
-  if (nt) k_batch_step<P, BLK><<<nt, BLK, WS_BYTES, B->stream>>>(B->dE, B->dT, s);
+  const int nt = (int)B->hT.size(), nf = (int)B->hF.size(), n2 = B->nT2;
+  if constexpr (sizeof(P) == 8) {
+    if (n2) k_batch_step<P, BLK, true><<<n2, BLK, WS_BYTES, B->stream>>>(B->dE, B->dT, s);
+  }
+  if (nt > n2)
+    k_batch_step<P, BLK, false><<<nt - n2, BLK, WS_BYTES, B->stream>>>(B->dE, B->dT + n2, s);
   if (nf) k_batch_fill<P><<<nf, 256, 0, B->stream>>>(B->dE, B->dF, s);
   return last_launch();
 }
@@ -791,9 +796,11 @@ int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precisio
   if (precision != LBM39_FP64 && precision != LBM39_MIXED) return LBM39_ERR_ARG;
   static bool attr = false;
   if (!attr) {
-    CUDA_OK(cudaFuncSetAttribute(k_batch_step<double, BLK>,
+    CUDA_OK(cudaFuncSetAttribute(k_batch_step<double, BLK, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_BYTES));
-    CUDA_OK(cudaFuncSetAttribute(k_batch_step<float, BLK>,
+    CUDA_OK(cudaFuncSetAttribute(k_batch_step<double, BLK, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_BYTES));
+    CUDA_OK(cudaFuncSetAttribute(k_batch_step<float, BLK, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_BYTES));
     attr = true;
   }
@@ -830,6 +837,7 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
   }
   if (cells > B->maxcells) return LBM39_ERR_ARG;
   B->hE.clear(); B->hT.clear(); B->hF.clear(); B->lats.clear(); B->tend.clear();
+  std::vector<Tile> full;  // tiles of lattices with the full 13-constraint solve
   for (int j = 0; j < n; ++j) {
     lbm39_lattice* L = lattices[j];
     BatchEntry e;
@@ -839,10 +847,14 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
     B->hE.push_back(e);
     B->lats.push_back(L);
     B->tend.push_back(t_end[j]);
-    for (long long c = 0; c < L->N; c += BLK) B->hT.push_back(Tile{j, 0, c});
+    // the nine-constraint (z-mirror) tiles first: they take their own instantiation
+    std::vector<Tile>& dst = (!L->mixed && L->desc.d2) ? B->hT : full;
+    for (long long c = 0; c < L->N; c += BLK) dst.push_back(Tile{j, 0, c});
     if (L->fills)
       for (long long c = 0; c < L->N; c += 256) B->hF.push_back(Tile{j, 0, c});
   }
+  B->nT2 = (int)B->hT.size();
+  B->hT.insert(B->hT.end(), full.begin(), full.end());
   if ((long long)B->hT.size() > B->maxtiles || (long long)B->hF.size() > B->maxftiles)
     return LBM39_ERR_ARG;
   if (n) {
