@@ -55,19 +55,27 @@ WORKLOADS = {
 # FP64 arithmetic of one fluid-cell update as executed by the step kernel, from ncu
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL) on two workloads with different
 # Newton work: A + B * (Newton updates per cell).  See profiles/.
-FP64_FLOPS_MODEL = {"fp64": (685.0, 2547.0), "mixed": (542.0, 1051.0),
-                    # the nine-constraint (z-mirror) solve of lattices one cell thick in z
-                    "fp64_2d": (650.0, 1470.0),
-                    # FP64 storage with the single-precision Newton direction (root finder 2):
-                    # the FP64 path's per-cell part and the 128^3 box's count (4870 flops per
-                    # cell at 3.99 updates per cell)
-                    "fp64_fp32dir": (685.0, 1049.0)}
+FP64_FLOPS_MODEL = {
+    # the 128^3 box at rms Ma 0.8 (3.97 updates per cell: 10471 flops per cell) and 0.3
+    # (3.21: 8589)
+    "fp64": (696.0, 2461.0),
+    "mixed": (542.0, 1051.0),
+    # the nine-constraint (z-mirror) solve of lattices one cell thick in z: the airfoil at
+    # 0.025 updates per cell and a quasi-2-D box at 3.13, with an earlier factorisation that
+    # formed 36 more DMULs per update (an upper bound now)
+    "fp64_2d": (650.0, 1470.0),
+    # FP64 storage with the single-precision Newton direction (root finder 2): the FP64 path's
+    # per-cell part and the 128^3 box's count (4869 flops per cell at 3.99 updates per cell)
+    "fp64_fp32dir": (696.0, 1046.0)}
 # DRAM bytes (read + write) per launch of the step kernel from ncu, per workload and
 # precision, with the hash of the step kernel's code they were captured with; reported as
-# null once that code differs (profiles/ has the captures).  The 256^3 figure is the 128^3
-# capture scaled by the cell count (x 8; the same per-cell work, both far beyond L2).
-NCU_TRAFFIC = {"kernel_hash": "54b5fc576d5ef072",
-               "gb_per_launch": {"box128/fp64": 5.655, "box256/fp64": 45.24}}
+# null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are
+# the 128^3 captures scaled by the cell count (x 8, x 27; the same per-cell work, all far
+# beyond L2).
+NCU_TRAFFIC = {"kernel_hash": "5fde5998f4a66b88",
+               "gb_per_launch": {"box128/fp64": 6.048, "box256/fp64": 48.38,
+                                 "box128/mixed": 3.028, "box256/mixed": 24.22,
+                                 "box384/mixed": 81.75}}
 # The sources the step kernels and their launches are built from (the serving-form kernels
 # in batch.cuh are not among them).
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
@@ -76,9 +84,9 @@ KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels
 # launch (per lattice side n of the n x n x 1 workload; null once the code differs).
 POLY_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                 "poly_eq.cuh", "poly.cu")
-POLY_NCU_TRAFFIC = {"kernel_hash": "16d713ebb5a1bc7d",
+POLY_NCU_TRAFFIC = {"kernel_hash": "2e50b51902d766de",
                     # 2048: the 1024 capture scaled by the cell count (both exceed L2)
-                    "gb_per_launch": {"1024": 1.272, "2048": 5.087}}
+                    "gb_per_launch": {"1024": 1.271, "2048": 5.082}}
 
 
 def source_code_text(text: str) -> str:
