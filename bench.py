@@ -60,10 +60,10 @@ FP64_FLOPS_MODEL = {
     # (3.21: 8589)
     "fp64": (696.0, 2461.0),
     "mixed": (542.0, 1051.0),
-    # the nine-constraint (z-mirror) solve of lattices one cell thick in z: the airfoil at
-    # 0.025 updates per cell and a quasi-2-D box at 3.13, with an earlier factorisation that
-    # formed 36 more DMULs per update (an upper bound now)
-    "fp64_2d": (650.0, 1470.0),
+    # the nine-constraint (z-mirror) solve of lattices one cell thick in z: the 2048x1024
+    # airfoil at 0.018 updates per cell (686 flops per cell) and the quasi-2-D 2048x1024 box
+    # at 3.26 (5129)
+    "fp64_2d": (661.0, 1369.0),
     # FP64 storage with the single-precision Newton direction (root finder 2): the FP64 path's
     # per-cell part and the 128^3 box's count (4869 flops per cell at 3.99 updates per cell)
     "fp64_fp32dir": (696.0, 1046.0)}
