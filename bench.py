@@ -56,9 +56,9 @@ WORKLOADS = {
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL) on two workloads with different
 # Newton work: A + B * (Newton updates per cell).  See profiles/.
 FP64_FLOPS_MODEL = {
-    # the 128^3 box at rms Ma 0.8 (3.97 updates per cell: 10471 flops per cell) and 0.3
-    # (3.21: 8589)
-    "fp64": (696.0, 2461.0),
+    # the 128^3 box at rms Ma 0.8 (3.97 updates per cell: 10509 flops per cell) and 0.3
+    # (3.21: 8619)
+    "fp64": (691.0, 2472.0),
     "mixed": (542.0, 1051.0),
     # the nine-constraint (z-mirror) solve of lattices one cell thick in z: the 2048x1024
     # airfoil at 0.018 updates per cell (686 flops per cell) and the quasi-2-D 2048x1024 box
@@ -66,7 +66,7 @@ FP64_FLOPS_MODEL = {
     "fp64_2d": (661.0, 1369.0),
     # FP64 storage with the single-precision Newton direction (root finder 2): the FP64 path's
     # per-cell part and the 128^3 box's count (4869 flops per cell at 3.99 updates per cell)
-    "fp64_fp32dir": (696.0, 1046.0)}
+    "fp64_fp32dir": (691.0, 1047.0)}
 # DRAM bytes (read + write) per launch of the step kernel from ncu, per workload and
 # precision, with the hash of the step kernel's code they were captured with; reported as
 # null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are

@@ -291,6 +291,45 @@ __device__ __forceinline__ void ldlt_apply(const T (&J)[N * (N + 1) / 2], const 
   });
 }
 
+// Position of L_ik (i > k, k < KS) when the first KS columns of L are parked in
+// a workspace array column after column.
+template <int N>
+constexpr int parked(int i, int k) {
+  int off = 0;
+  for (int c = 0; c < k; ++c) off += N - 1 - c;
+  return off + (i - k - 1);
+}
+
+// ldlt_apply with the first KS columns of L read from the workspace array P
+// (parked there by the caller), the others from J.
+template <int N, int KS, int BLK>
+__device__ __forceinline__ void ldlt_apply_parked(const double (&J)[N * (N + 1) / 2],
+                                                  const double (&rd)[N], WS<BLK> P,
+                                                  double (&b)[N]) {
+  static_for<1, N>([&](auto II) {  // L y = b
+    constexpr int i = decltype(II)::value;
+    double a = b[i];
+    static_for<0, i>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      const double l = k < KS ? P[parked<N>(i, k)] : J[tri(i, k)];
+      a = fma(-l, b[k], a);
+    });
+    b[i] = a;
+  });
+#pragma unroll
+  for (int i = 0; i < N; ++i) b[i] *= rd[i];  // D z = y
+  static_for<0, N - 1>([&](auto II) {  // L^T x = z
+    constexpr int i = N - 2 - decltype(II)::value;
+    double a = b[i];
+    static_for<i + 1, N>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      const double l = i < KS ? P[parked<N>(k, i)] : J[tri(k, i)];
+      a = fma(-l, b[k], a);
+    });
+    b[i] = a;
+  });
+}
+
 // In-place LDL^T of a packed symmetric N x N J and the solve J x = b (b
 // overwritten by x).  False if a pivot is not positive.
 template <class T, int N = NM>
@@ -313,9 +352,26 @@ __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
     if constexpr (D2) gen::moments2d<double>(F, s, J);
     else gen::moments<double>(F, s, J);
     const bool ok = ldlt_factor<double, N>(J, rd);
+    if constexpr (D2) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) b[k] = dl[k];  // the right-hand side, once J is factored
-    ldlt_apply<double, N>(J, rd, b);
+      for (int k = 0; k < N; ++k) b[k] = dl[k];  // the right-hand side, once J is factored
+      ldlt_apply<double, N>(J, rd, b);
+    } else {
+      // The 13x13 solve needs L, D and b at once (more than the registers hold): the
+      // first three columns of L (33 values) wait in F's workspace slots, which the next
+      // evaluation overwrites before anything reads them.
+      constexpr int KS = 3;
+      static_for<0, KS>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        static_for<k + 1, N>([&](auto II) {
+          constexpr int i = decltype(II)::value;
+          F[parked<N>(i, k)] = J[tri(i, k)];
+        });
+      });
+#pragma unroll
+      for (int k = 0; k < N; ++k) b[k] = dl[k];
+      ldlt_apply_parked<N, KS, BLK>(J, rd, F, b);
+    }
 #pragma unroll
     for (int k = 0; k < N; ++k) dl[k] = b[k];
     return ok;
