@@ -737,6 +737,11 @@ def main():
                          "fp32dir: Newton with a single-precision direction)")
     ap.add_argument("--start-at", type=int, default=0,
                     help="step the lattice to this time before the warm-up (developed flows)")
+    ap.add_argument("--checkpoint-out", default=None,
+                    help="after --start-at, save the lattice's checkpoint (lbm39_save) to this file")
+    ap.add_argument("--checkpoint-in", default=None,
+                    help="start from a checkpoint saved with --checkpoint-out for the same "
+                         "workload and options (instead of --start-at)")
     ap.add_argument("--newton-tol", type=float, default=1e-12,
                     help="stopping tolerance of the constraint solve (max |G_k| / rho)")
     args = ap.parse_args()
@@ -781,9 +786,13 @@ def main():
     N = s.ncells
     st_init = L.stats()
     fluid = st_init.fluid_cells
+    if args.checkpoint_in:
+        L.restore(torch.load(args.checkpoint_in).to(f"cuda:{local}"))
     while L.time < args.start_at:
         L.step(min(500, args.start_at - L.time))
         L.sync()
+    if args.checkpoint_out:
+        torch.save(L.checkpoint().cpu(), args.checkpoint_out)
 
     L.step(args.warmup)
     L.sync()
@@ -891,7 +900,7 @@ def main():
     sections = set() if args.sections == "none" else set(args.sections.split(","))
     suite = (args.workload == "box256" and args.precision == "fp64" and world == 1
              and args.root_finder == "newton" and args.newton_tol == 1e-12
-             and args.start_at == 0)
+             and args.start_at == 0 and not args.checkpoint_in)
     serving = airfoil = solvers = None
     if suite and "precision" in sections:
         form = precision_form_section(args, local, s, (headline_state, value))
@@ -913,7 +922,7 @@ def main():
     if rank == 0:
         config = {"workload": workload_text(args), "precision": args.precision,
                   "root_finder": args.root_finder, "newton_tol": args.newton_tol,
-                  "timed_from_step": args.start_at + args.warmup,
+                  "timed_from_step": st0.time,
                   "cells": N, "fluid_cells": int(fluid),
                   "fluid_mlups": round(fluid * args.steps * world / (elapsed_ms * 1e-3) / 1e6, 3),
                   "l2": "inputs larger than L2 (%.2f GB of populations)" % (

@@ -543,8 +543,11 @@ __device__ NewtonResult newton_chord(WS<BLK> w, const Phys& ph, int maxit, bool 
 // sum_i F_i [1, xi_i, |xi_i|^2] = [1, u, u^2 + D T]: it exists far beyond that
 // cone and conserves mass, momentum and energy (g^eq = (2 C_v - D) T f^eq as
 // for the full equilibrium).  Same damped Newton iteration and stopping rule
-// as the full solve, from the Gaussian start.  Rare, so written for size: a
-// rolled loop over the velocities and a non-inlined function.
+// as the full solve, from the Gaussian start.  The five multipliers enter the
+// exponent as the embedding (mu_0, mu_x, mu_y, mu_z, mu_4, mu_4, mu_4, 0...) of
+// the 13, so the evaluation uses the full solve's generated exponent and
+// moment sums, and those 13 sums give the 5 x 5 Jacobian but for one entry,
+// sum_i F_i |xi_i|^4.  A non-inlined function (one copy of this code).
 constexpr int N5 = 5;
 constexpr int FALLBACK_MAXIT = 50;
 constexpr double FALLBACK_TOL = 1e-12;
@@ -563,54 +566,62 @@ constexpr double FALLBACK_TOL = 1e-12;
 constexpr int RETRY_MAXIT = 3;
 constexpr int RETRY_PERIOD = 8;  // a power of two
 
-// F = exp(phi5 . (mu - t dl)) (t = 0: mu itself) and G = sum_i F_i phi5(xi_i) - m5.
+// F = exp(phi5 . (mu - t dl)) (t = 0: mu itself), the 13 sums s_k = sum_i F_i
+// phi_k(xi_i) at that point, and G = sum_i F_i phi5(xi_i) - m5 (phi5 = [1, xi,
+// |xi|^2], so its sums are s_0..s_3 and s_4 + s_5 + s_6).
 template <int BLK>
 __device__ __forceinline__ void eval5(WS<BLK> mu, WS<BLK> dl, double t, WS<BLK> F,
-                                      const double (&m5)[N5], double (&G)[N5]) {
-  double l[N5];
+                                      const double (&m5)[N5], double (&G)[N5],
+                                      double (&s)[NM]) {
+  double v[N5];
 #pragma unroll
-  for (int k = 0; k < N5; ++k) l[k] = t == 0.0 ? mu[k] : fma(-t, dl[k], mu[k]);
-  double s[N5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll 1
-  for (int i = 0; i < Q; ++i) {
-    const double cx = kCX[i], cy = kCY[i], cz = kCZ[i];
-    const double c2 = cx * cx + cy * cy + cz * cz;
-    const double Fi = exp_tang(l[0] + l[1] * cx + l[2] * cy + l[3] * cz + l[4] * c2);
-    F[i] = Fi;
-    s[0] += Fi;
-    s[1] = fma(Fi, cx, s[1]);
-    s[2] = fma(Fi, cy, s[2]);
-    s[3] = fma(Fi, cz, s[3]);
-    s[4] = fma(Fi, c2, s[4]);
+  for (int k = 0; k < N5; ++k) v[k] = t == 0.0 ? mu[k] : fma(-t, dl[k], mu[k]);
+  const double l[NM] = {v[0], v[1], v[2], v[3], v[4], v[4], v[4], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double x[Q];
+  gen::exponents(l, x);
+  int wide = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
+  if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
+#pragma unroll
+    for (int i = 0; i < Q; ++i) F[i] = x[i];
+    exp_all_slow<BLK>(F.p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) x[i] = F[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      x[i] = exp_tang_core(x[i]);
+      F[i] = x[i];
+    }
   }
-#pragma unroll
-  for (int k = 0; k < N5; ++k) G[k] = s[k] - m5[k];
+  gen::moments_s<double>(x, s);
+  G[0] = s[0] - m5[0];
+  G[1] = s[1] - m5[1];
+  G[2] = s[2] - m5[2];
+  G[3] = s[3] - m5[3];
+  G[4] = ((s[4] + s[5]) + s[6]) - m5[4];
 }
 
 // Newton direction of the fallback: J = sum_i F_i phi5 phi5^T (symmetric
-// positive definite), J d = b by elimination without pivoting; false if a
-// pivot is not positive.
+// positive definite) from the 13 sums s of the same F and sum_i F_i |xi_i|^4,
+// J d = b by elimination without pivoting; false if a pivot is not positive.
 template <int BLK>
-__device__ __forceinline__ bool direction5(WS<BLK> F, double (&b)[N5]) {
-  double A[N5][N5];
-#pragma unroll
-  for (int k = 0; k < N5; ++k)
-#pragma unroll
-    for (int l = 0; l < N5; ++l) A[k][l] = 0.0;
-#pragma unroll 1
-  for (int i = 0; i < Q; ++i) {
-    const double cx = kCX[i], cy = kCY[i], cz = kCZ[i];
-    const double p[N5] = {1.0, cx, cy, cz, cx * cx + cy * cy + cz * cz};
-    const double Fi = F[i];
-#pragma unroll
-    for (int k = 0; k < N5; ++k)
-#pragma unroll
-      for (int l = 0; l <= k; ++l) A[k][l] = fma(Fi * p[k], p[l], A[k][l]);
-  }
-#pragma unroll
-  for (int k = 0; k < N5; ++k)
-#pragma unroll
-    for (int l = k + 1; l < N5; ++l) A[k][l] = A[l][k];
+__device__ __forceinline__ bool direction5(WS<BLK> F, const double (&s)[NM], double (&b)[N5]) {
+  double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // sum of F_i over each |xi|^2 in {1,3,4,8,9}
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int r = c2(i);
+    constexpr int k = r == 1 ? 0 : r == 3 ? 1 : r == 4 ? 2 : r == 8 ? 3 : 4;
+    q[k] += F[i];
+  });
+  const double e4 = fma(81.0, q[4], fma(64.0, q[3], fma(16.0, q[2], fma(9.0, q[1], q[0]))));
+  const double e2 = (s[4] + s[5]) + s[6];
+  double A[N5][N5] = {{s[0], s[1], s[2], s[3], e2},
+                      {s[1], s[4], s[7], s[8], s[10]},
+                      {s[2], s[7], s[5], s[9], s[11]},
+                      {s[3], s[8], s[9], s[6], s[12]},
+                      {e2, s[10], s[11], s[12], e4}};
   bool ok = true;
 #pragma unroll
   for (int c = 0; c < N5; ++c) {
@@ -656,7 +667,7 @@ template <int BLK>
 __device__ __noinline__ int fallback_equilibrium(WS<BLK> w, double T, const double* warm) {
   WS<BLK> F = w.at(WS_E), mu = w.at(WS_M), dl = w.at(WS_DL);
   const double m5[N5] = {1.0, mu[1], mu[2], mu[3], mu[4] + mu[5] + mu[6]};
-  double G[N5];
+  double G[N5], s[NM];
   if (warm) {
 #pragma unroll
     for (int k = 0; k < N5; ++k) mu[k] = warm[k];
@@ -665,19 +676,16 @@ __device__ __noinline__ int fallback_equilibrium(WS<BLK> w, double T, const doub
     mu[0] = 0.0;
     mu[1] = m5[1] * it; mu[2] = m5[2] * it; mu[3] = m5[3] * it;
     mu[4] = -0.5 * it;
-    eval5<BLK>(mu, dl, 0.0, F, m5, G);
-    double s = 0.0;
-#pragma unroll 1
-    for (int i = 0; i < Q; ++i) s += F[i];
-    mu[0] = -log(s);
+    eval5<BLK>(mu, dl, 0.0, F, m5, G, s);
+    mu[0] = -log(s[0]);  // normalises sum_i F_i to 1
   }
-  eval5<BLK>(mu, dl, 0.0, F, m5, G);
+  eval5<BLK>(mu, dl, 0.0, F, m5, G, s);
   int n = 0, ls = 0;
   bool polished = false, first = true;
   double t = 0.0, s0 = 0.0;
   for (;;) {
     if (!first) {
-      eval5<BLK>(mu, dl, t, F, m5, G);
+      eval5<BLK>(mu, dl, t, F, m5, G, s);
       double ss = 0.0;
 #pragma unroll
       for (int k = 0; k < N5; ++k) ss = fma(G[k], G[k], ss);
@@ -704,7 +712,7 @@ __device__ __noinline__ int fallback_equilibrium(WS<BLK> w, double T, const doub
     double b[N5];
 #pragma unroll
     for (int k = 0; k < N5; ++k) b[k] = G[k];
-    if (!direction5<BLK>(F, b)) return 1;
+    if (!direction5<BLK>(F, s, b)) return 1;
 #pragma unroll
     for (int k = 0; k < N5; ++k) dl[k] = b[k];
     polished = r < FALLBACK_TOL;

@@ -388,9 +388,9 @@ __device__ __forceinline__ void eval_at_lam(WS<BLK> w) {
 
 // Where the 13-moment solve failed or took no update: the fallback's
 // multipliers embedded in lam and marked (lam unchanged but unmarked if the
-// fallback fails too), and F =
-// exp(Phi lam) evaluated as the full solve does, so the cached F stays exact
-// (for an embedding it is the fallback equilibrium up to rounding).  retry:
+// fallback fails too), and F = exp(Phi lam) exactly as the full solve
+// evaluates it (the fallback evaluates the embedding with the same exponents
+// and exponential), so the cached F stays exact.  retry:
 // the cell came in with a fallback embedding, whose five multipliers (still in
 // the stored state) start the fallback.
 // state, Np: the solver-state planes (Desc::lam) and their stride.
@@ -411,10 +411,12 @@ __device__ __noinline__ void fallback_cell(const double* state, long long Np, lo
 #pragma unroll
     for (int k = 7; k < NM; ++k) lam[k] = 0.0;
     lam[9] = -0.0;  // the embedding mark: on the fallback
+    // F already holds exp(Phi lam): the fallback's last evaluation was at this
+    // embedding, with the full solve's exponents and exponential
   } else {
     lam[9] = lam[9] + 0.0;  // the fallback failed too: not on the fallback
+    eval_at_lam<BLK>(w);    // F = exp(Phi lam), the cached value the next solve starts from
   }
-  eval_at_lam<BLK>(w);  // F = exp(Phi lam), the cached value the next solve starts from
 }
 
 // Newton budget of a cell on the fallback at time step t: RETRY_MAXIT on the
