@@ -72,10 +72,10 @@ FP64_FLOPS_MODEL = {
 # null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are
 # the 128^3 captures scaled by the cell count (x 8, x 27; the same per-cell work, all far
 # beyond L2).
-NCU_TRAFFIC = {"kernel_hash": "3c76d14747edb8e7",
-               "gb_per_launch": {"box128/fp64": 4.762, "box256/fp64": 38.09,
+NCU_TRAFFIC = {"kernel_hash": "0d9755488c8f81df",
+               "gb_per_launch": {"box128/fp64": 4.759, "box256/fp64": 38.07,
                                  "box128/mixed": 3.028, "box256/mixed": 24.22,
-                                 "box384/mixed": 81.76}}
+                                 "box384/mixed": 81.75}}
 # The sources the step kernels and their launches are built from (the serving-form kernels
 # in batch.cuh are not among them).
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
@@ -84,9 +84,9 @@ KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels
 # launch (per lattice side n of the n x n x 1 workload; null once the code differs).
 POLY_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
                 "poly_eq.cuh", "poly.cu")
-POLY_NCU_TRAFFIC = {"kernel_hash": "ec8ee5e79d2d4892",
+POLY_NCU_TRAFFIC = {"kernel_hash": "02dc9070eca147c2",
                     # 2048: the 1024 capture scaled by the cell count (both exceed L2)
-                    "gb_per_launch": {"1024": 1.271, "2048": 5.086}}
+                    "gb_per_launch": {"1024": 1.272, "2048": 5.087}}
 
 
 def source_code_text(text: str) -> str:

@@ -73,3 +73,35 @@ def test_served_results_match_the_oracle():
         assert failed == 0
         d = rel_diffs(rep.results[r.rid], o.macros(st), r.setup.mask, r.setup.gamma)
         assert max(d) <= TOL, (r.setup.name, d)
+
+
+def test_packed_mix_of_constraint_systems():
+    """A batch that holds lattices of both constraint systems -- one-cell-thick shear layers and
+    tubes (the nine-constraint z-mirror solve) and 3-D boxes (all 13) -- runs each set with its
+    own packed instantiation; every result equals the lattice run alone, bit for bit."""
+    from paper_1910_13515_gb300 import build
+    build.build()
+    from paper_1910_13515_gb300.lattice import Lattice
+    from paper_1910_13515_gb300.serve import GpuBackend, Scheduler
+
+    rng = np.random.default_rng(23)
+    reqs = []
+    for rid in range(6):
+        steps = int(rng.integers(10, 30))
+        if rid % 3 == 0:
+            s = inputs.box(seed=rid, shape=(6, 7, 9), steps=steps, mach_rms=0.5)
+        elif rid % 3 == 1:
+            s = inputs.shear_layer(16, 1.2, steps=steps, seed=rid)
+        else:
+            s = inputs.random_riemann(rng, 200, 300, steps=steps)
+        reqs.append(inputs.Request(rid, 0.001 * rid, s))
+    be = GpuBackend(precision=0, max_lattices=8, max_cells=1 << 16, graph_steps=4)
+    rep = Scheduler(be, budget_bytes=1 << 34, max_resident=8, chunk_steps=8).run(reqs)
+    be.close()
+    assert rep.max_resident >= 3
+    for r in reqs:
+        L = Lattice.from_setup(r.setup)
+        L.step(r.setup.steps)
+        assert L.sync() == 0
+        for a, b in zip(L.read_numpy(), rep.results[r.rid]):
+            assert np.array_equal(a, b), r.setup.name
