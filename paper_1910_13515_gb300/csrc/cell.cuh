@@ -116,16 +116,6 @@ __device__ __forceinline__ float view_float(double x) {
 // Biased exponent field of a double (bits 52..62 in place, as an int).
 __device__ __forceinline__ int exp_field(double x) { return __double2hiint(x) & 0x7ff00000; }
 
-// Exact float -> double by integer operations (normal floats and zero; other
-// values take the conversion instruction).
-__device__ __forceinline__ double exact_double(float v) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned e = (b >> 23) & 0xff;
-  if (e == 0 || e == 255) return (double)v;
-  const unsigned hi = (b & 0x80000000u) | ((e + (1023 - 127)) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
-}
-
 // exp of the 39 exponents parked in F (stride BLK), by CUDA's exp: the rare
 // path for arguments outside exp_tang_core's range.
 template <int BLK>
@@ -385,7 +375,7 @@ __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
     for (int k = 0; k < N; ++k) bf[k] = trunc_float(dl[k]);
     const bool ok = ldlt_solve<float, N>(J, bf);
 #pragma unroll
-    for (int k = 0; k < N; ++k) dl[k] = exact_double(bf[k]);
+    for (int k = 0; k < N; ++k) dl[k] = (double)bf[k];
     return ok;
   }
 }
@@ -781,7 +771,7 @@ __device__ __forceinline__ bool screen_undecided(float s39, int emin, int emax, 
 
 // The screen of the precision form, whose terms are |d_i| r_i with d_i = f~_i - rf_i
 // the float difference of the stored deviation and the equilibrium's, rf_i =
-// round_float(f^eq_i - f_ref_i), and r_i = rcp32(rho~ F~_i).  With u = 2^-24: d_i is
+// f^eq_i - f_ref_i rounded to the nearest float, and r_i = rcp32(rho~ F~_i).  With u = 2^-24: d_i is
 // within u|d_i| of the exact difference, r_i within 7u of 1/f^eq_i (two float views 2u
 // each, the product u, rcp32 2u), the product adds u, and four interleaved partial sums
 // of at most 10 terms add at most 12u s: |s32 - s| <= 21u s32 to first order.  True when

@@ -29,7 +29,7 @@ __device__ __forceinline__ void gather_f(const Desc& d, long long cell, double (
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if constexpr (sizeof(P) == 8) f[i] = h[i];
-    else f[i] = exact_double(h[i]) + d.href[i];
+    else f[i] = (double)h[i] + d.href[i];
   }
 }
 

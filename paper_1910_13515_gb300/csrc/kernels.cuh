@@ -157,11 +157,11 @@ __device__ __forceinline__ Raw gather_raw(const Desc& d, long long cell, const N
     double hd[Q];
     gather<ODD, P>(d, cell, nb, 0, h);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
+    for (int i = 0; i < Q; ++i) hd[i] = (double)h[i];
     gen::f_moments<double>(hd, r.rho, r.jx, r.jy, r.jz, r.e2);
     gather<ODD, P>(d, cell, nb, Q, h);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) hd[i] = exact_double(h[i]);
+    for (int i = 0; i < Q; ++i) hd[i] = (double)h[i];
     gs = gen::g_sum<double>(hd);
     r.rho += d.mref[0]; r.jx += d.mref[1]; r.jy += d.mref[2]; r.jz += d.mref[3];
     gs += d.mref[4];
@@ -174,17 +174,6 @@ template <bool ODD, class P>
 __device__ __forceinline__ Macro gather_moments(const Desc& d, long long cell, const Nbr& nb) {
   const Raw r = gather_raw<ODD, P>(d, cell, nb);
   return macro_from_moments(r.rho, r.jx, r.jy, r.jz, r.e2, d.ph.inv_2cv);
-}
-
-// Round-to-nearest double -> float by integer operations (normal range;
-// other values take the conversion instruction).
-__device__ __forceinline__ float round_float(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long r = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
-  const int e = (int)((r >> 52) & 0x7ff) - 896;
-  if (e <= 0 || e >= 255) return __double2float_rn(x);
-  return __uint_as_float((unsigned)((b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
-                         (unsigned)((r >> 29) & 0x7fffffu));
 }
 
 // Phase C: gather again, Knudsen sensor (Eq. DeltaAvg, f only), tau_eff =
@@ -290,7 +279,7 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double Fi = F[i];
-      f[i] -= round_float(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
+      f[i] -= __double2float_rn(fma(rho, Fi, -__ldg(href + i)));  // f~ - (f^eq - f_ref)
       acc[i & 3] += fabsf(f[i]) * rcp32(rho32 * trunc_float(Fi));
     }
     const float s32 = (acc[0] + acc[1]) + (acc[2] + acc[3]);
@@ -302,8 +291,8 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const double feq = rho * F[i];
-        const float rf = round_float(fma(rho, F[i], -__ldg(href + i)));
-        s += fabs(exact_double(fs[i]) - exact_double(rf)) / feq;  // the difference is exact
+        const float rf = __double2float_rn(fma(rho, F[i], -__ldg(href + i)));
+        s += fabs((double)fs[i] - (double)rf) / feq;  // the difference is exact
       }
       eps = s * (1.0 / Q);
     }
@@ -319,7 +308,7 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
     if constexpr (!PR) {
       static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const float qg = round_float(fma(cgr, F[i], -__ldg(href + Q + i)));
+        const float qg = __double2float_rn(fma(cgr, F[i], -__ldg(href + Q + i)));
         push<ODD, P, i>(d, cell, nb, Q, fmaf(-omega, g[i] - qg, g[i]));
       });
     } else {
@@ -329,7 +318,7 @@ __device__ __forceinline__ int relax_push(const Desc& d, long long cell, const N
       float e[Q], qx = 0.0f, qy = 0.0f, qz = 0.0f;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        e[i] = g[i] - round_float(fma(cgr, F[i], -__ldg(href + Q + i)));  // g - g^eq
+        e[i] = g[i] - __double2float_rn(fma(cgr, F[i], -__ldg(href + Q + i)));  // g - g^eq
         const float cx = (float)kCX[i] - ux, cy = (float)kCY[i] - uy, cz = (float)kCZ[i] - uz;
         const float w = 0.5f * fmaf(cx * cx + cy * cy + cz * cz, f[i], e[i]);
         qx = fmaf(cx, w, qx);
@@ -476,7 +465,7 @@ __global__ void __launch_bounds__(BLK) k_step(Desc d) {
 template <class P>
 __device__ __forceinline__ P to_store(const Desc& d, int j, double v) {
   if constexpr (sizeof(P) == 8) return v;
-  else return round_float(v - __ldg(d.href + j));
+  else return __double2float_rn(v - __ldg(d.href + j));
 }
 
 // Equilibrium initial condition of fluid cells in [c0, c0 + len): inputs are
