@@ -41,7 +41,8 @@ typedef struct {
   double rho_inf, u_inf[3], T_inf; /* far-field state for freestream cells */
   double prandtl;      /* Prandtl number; 0 or 1: Pr = 1, plain BGK (Sec. 3) */
   int32_t root_finder; /* 0: Newton-Raphson (Sec. 3); 1: chord-Newton hybrid; 2: Newton with a
-                          float direction (other root finders: Sec. 6 outlook) */
+                          float direction; 3: 2 after a single-precision start (other root
+                          finders: Sec. 6 outlook) */
 } o39_params;
 
 typedef struct {
@@ -510,6 +511,97 @@ int o39_newton_fp32dir(const double *m, double *lam, double tol, int maxit, int 
   return status;
 }
 
+/* Newton started in single precision (a fourth root finder; the outlook,
+ * Sec. 6, names other root finders).  reading: from a warm start the first
+ * Newton steps only need the residual to a few digits, which float
+ * arithmetic gives; the last digits need double precision.  So:
+ *  1. from F0 = exp(Phi lam) (double, rounded to float), Newton steps in float
+ *     on the change delta of the multipliers: F_i = F0_i expf(phi(xi_i).delta),
+ *     G = sum_i F_i phi(xi_i) - m, J = sum_i F_i phi phi^T, delta <- delta - J^{-1} G,
+ *     every operation in float, while max|G| >= START32_THETA and at most
+ *     START32_MAXIT times; a step is kept only if it lowers max|G| (otherwise
+ *     this phase ends there, with the last kept delta);
+ *  2. lam <- lam + delta in double, then o39_newton_fp32dir from there, whose
+ *     double-precision residual decides convergence as for every root finder.
+ * A solve with no budget (maxit = 0: a cell on the fallback off a retry step)
+ * takes no float step either.  *n32_out: the float steps kept. */
+#define START32_THETA 1e-4f
+#define START32_MAXIT 4
+
+static void eval_float(const float *F0, const float *delta, const float *mf, float *F,
+                       float *G) {
+  for (int i = 0; i < Q; ++i) {
+    double phi[NM];
+    basis_i(i, phi);
+    float e = 0.0f;
+    for (int k = 0; k < NM; ++k) e += delta[k] * (float)phi[k];
+    F[i] = F0[i] * expf(e);
+  }
+  for (int k = 0; k < NM; ++k) {
+    float s = 0.0f;
+    for (int i = 0; i < Q; ++i) {
+      double phi[NM];
+      basis_i(i, phi);
+      s += F[i] * (float)phi[k];
+    }
+    G[k] = s - mf[k];
+  }
+}
+
+static float maxabs_float(const float *v) {
+  float r = 0.0f;
+  for (int k = 0; k < NM; ++k) {
+    float a = fabsf(v[k]);
+    if (!(a <= r)) r = a;
+  }
+  return r;
+}
+
+int o39_newton_fp32start(const double *m, double *lam, double tol, int maxit, int min_upd,
+                         int *n_upd_out, int *n32_out, double *F) {
+  build_lattice();
+  int n32 = 0;
+  if (maxit > 0) {
+    double F0d[Q];
+    float F0[Q], mf[NM], delta[NM], Fc[Q], G[NM];
+    o39_feq_norm(lam, F0d);
+    for (int i = 0; i < Q; ++i) F0[i] = (float)F0d[i];
+    for (int k = 0; k < NM; ++k) { mf[k] = (float)m[k]; delta[k] = 0.0f; }
+    eval_float(F0, delta, mf, Fc, G);
+    float r = maxabs_float(G);
+    while (n32 < START32_MAXIT && r >= START32_THETA) {
+      float J[NM * NM], Ji[NM * NM], dt[NM], Ft[Q], Gt[NM];
+      for (int k = 0; k < NM; ++k)
+        for (int l = 0; l < NM; ++l) {
+          float s = 0.0f;
+          for (int i = 0; i < Q; ++i) {
+            double phi[NM];
+            basis_i(i, phi);
+            s += Fc[i] * (float)phi[k] * (float)phi[l];
+          }
+          J[k * NM + l] = s;
+        }
+      if (invert_float(J, Ji, NM) != 0) break;
+      for (int k = 0; k < NM; ++k) {
+        float s = 0.0f;
+        for (int l = 0; l < NM; ++l) s += Ji[k * NM + l] * G[l];
+        dt[k] = delta[k] - s;
+      }
+      eval_float(F0, dt, mf, Ft, Gt);
+      float rt = maxabs_float(Gt);
+      if (!(rt < r)) break;
+      memcpy(delta, dt, sizeof dt);
+      memcpy(Fc, Ft, sizeof Ft);
+      memcpy(G, Gt, sizeof Gt);
+      r = rt;
+      ++n32;
+    }
+    for (int k = 0; k < NM; ++k) lam[k] += (double)delta[k];
+  }
+  if (n32_out) *n32_out = n32;
+  return o39_newton_fp32dir(m, lam, tol, maxit, min_upd, n_upd_out, F);
+}
+
 /* The root finder the run parameters select. */
 static int solve13(const o39_params *p, const double *m, double *lam, int maxit, int *n_upd,
                    double *F) {
@@ -517,6 +609,8 @@ static int solve13(const o39_params *p, const double *m, double *lam, int maxit,
     return o39_newton_hybrid(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, NULL, F);
   if (p->root_finder == 2)
     return o39_newton_fp32dir(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
+  if (p->root_finder == 3)
+    return o39_newton_fp32start(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, NULL, F);
   return o39_newton(m, lam, p->newton_tol, maxit, p->newton_min_upd, n_upd, F);
 }
 

@@ -92,6 +92,8 @@ def lib():
         _lib.o39_newton_hybrid.restype = ctypes.c_int
         _lib.o39_newton_fp32dir.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib.o39_newton_fp32dir.restype = ctypes.c_int
+        _lib.o39_newton_fp32start.argtypes = [vp, vp, d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        _lib.o39_newton_fp32start.restype = ctypes.c_int
         _lib.o39_alpha.argtypes = [d, d]
         _lib.o39_alpha.restype = d
         _lib.o39_cell_macros.argtypes = [P, vp, vp, vp, vp, vp]
@@ -315,6 +317,18 @@ def equilibrium(cfg: Config, rho, u, T, maxit=200):
     st = lib().o39_equilibrium(ctypes.byref(p), float(rho), _p(_f64(u)), float(T), _p(feq),
                                _p(geq), _p(lam), int(maxit), None)
     return feq, geq, lam, st
+
+
+def newton_fp32start(m, lam0, tol=1e-12, maxit=30, min_upd=0):
+    """Newton with a single-precision direction after a single-precision start:
+    (lam, F, n_updates, n_float_steps, status); n_updates counts the double-precision ones."""
+    lam = _f64(lam0).copy()
+    F = np.zeros(Q)
+    nu = ctypes.c_int(0)
+    n32 = ctypes.c_int(0)
+    st = lib().o39_newton_fp32start(_p(_f64(m)), _p(lam), float(tol), int(maxit), int(min_upd),
+                                    ctypes.byref(nu), ctypes.byref(n32), _p(F))
+    return lam, F, nu.value, n32.value, st
 
 
 # ---------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-"""Pins of the oracle's chord-Newton hybrid root finder (lbm39 root_finder 1; the paper's outlook
+"""Pins of the oracle's other root finders (lbm39 root_finder 1-3; the paper's outlook
 names other root finders): it must land on the same constrained maximum-entropy equilibrium as
 Newton-Raphson -- the one the closed-form Maxwell-Boltzmann targets define, unique because the
 dual problem is strictly convex -- under the same stopping rule, forming fewer Jacobians."""
@@ -135,3 +135,75 @@ def test_lattice_run_with_the_fp32_direction_matches_newton(oracle):
         runs.append(oracle.macros(st))
     for x, y in zip(runs[0][:3], runs[1][:3]):
         assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
+
+
+def test_fp32_start_reaches_the_same_equilibrium(oracle):
+    """Newton after a single-precision start (root_finder 3): the float steps only move the
+    starting point, and the double-precision residual decides convergence, so it lands on the
+    Maxwell-Boltzmann moments to 1e-12 and on Newton's equilibrium from cold and warm starts."""
+    vel, _, _ = oracle.lattice()
+    for _ in range(200):
+        u, T = random_state(RNG)
+        m = mb_targets(u, T)
+        lam, F, n, n32, st = oracle.newton_fp32start(m, oracle.gaussian_guess(u, T), maxit=200)
+        assert st == 0
+        assert np.all(np.abs(moments(vel, F) - m) <= 1e-12 * np.maximum(1, np.abs(m)))
+        m2 = mb_targets(u + RNG.normal(scale=0.05, size=3), T + RNG.normal(scale=0.02))
+        l1, F1, k1, s1 = oracle.newton(m2, lam)
+        l3, F3, k3, n3, s3 = oracle.newton_fp32start(m2, lam)
+        assert s1 == 0 and s3 == 0
+        assert np.abs(F1 - F3).max() <= 1e-12 * F1.max()
+
+
+def test_fp32_start_saves_double_precision_updates(oracle):
+    """Warm starts a time step away in a fast flow (residuals ~1e-2): the float steps take the
+    residual to about 1e-4, and the double-precision updates that remain are at least a
+    quarter fewer than those of the same solver without the float start (root_finder 2).
+    (A residual near 1, where an undamped step overshoots, may take none: the damped
+    double-precision iteration then starts from the warm start itself.)"""
+    n2 = n3 = n32 = 0
+    for _ in range(200):
+        u, T = random_state(RNG)
+        lam0 = oracle.newton(mb_targets(u, T), oracle.gaussian_guess(u, T), maxit=200)[0]
+        m = mb_targets(u + RNG.normal(scale=0.1, size=3), T + RNG.normal(scale=0.03))
+        r0 = np.abs(oracle.residual(lam0, m)).max()
+        l2, F2, k2, s2 = oracle.newton_fp32dir(m, lam0)
+        l3, F3, k3, j3, s3 = oracle.newton_fp32start(m, lam0)
+        assert s2 == 0 and s3 == 0
+        assert np.abs(F2 - F3).max() <= 1e-12 * F2.max()
+        if 1e-4 <= r0 < 0.1:
+            assert j3 >= 1  # above the threshold, within reach of a full step: a float step
+        n2 += k2
+        n3 += k3
+        n32 += j3
+    assert n3 <= 0.75 * n2, (n3, n2)
+    assert n32 >= 200
+
+
+def test_fp32_start_leaves_converged_and_unbudgeted_solves_alone(oracle):
+    """A warm start already at the root takes no float step and no update; a solve with no
+    budget (a cell on the fallback off a retry step) takes no float step and keeps lambda."""
+    for _ in range(50):
+        u, T = random_state(RNG)
+        m = mb_targets(u, T)
+        lam = oracle.newton(m, oracle.gaussian_guess(u, T), maxit=200)[0]
+        l3, F3, k3, j3, s3 = oracle.newton_fp32start(m, lam)
+        assert (k3, j3, s3) == (0, 0, 0) and np.array_equal(l3, lam)
+        m2 = mb_targets(u + 0.1, T)
+        l4, F4, k4, j4, s4 = oracle.newton_fp32start(m2, lam, maxit=0)
+        assert (k4, j4, s4) == (0, 0, 1) and np.array_equal(l4, lam)
+
+
+def test_lattice_run_with_the_fp32_start_matches_newton(oracle):
+    s = inputs.box(seed=5, shape=(10, 10, 10))
+    runs = []
+    for rf in (0, 3):
+        cfg = oracle.Config(nx=s.nx, ny=s.ny, nz=s.nz, gamma=s.gamma, tau=s.tau,
+                            kn_sensor=s.kn_sensor, root_finder=rf)
+        st = oracle.init(cfg, s.mask, s.rho, s.u, s.T)
+        assert oracle.step(st, 20) == 0
+        runs.append((oracle.macros(st), st.stats.newton_updates))
+    (a, na), (b, nb) = runs
+    for x, y in zip(a[:3], b[:3]):
+        assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
+    assert nb < na  # fewer double-precision updates than Newton's
