@@ -54,19 +54,29 @@ WORKLOADS = {
 
 # FP64 arithmetic of one fluid-cell update as executed by the step kernel, from ncu
 # instruction counts (2 flops per DFMA, 1 per DADD/DMUL) on two workloads with different
-# Newton work: A + B * (Newton updates per cell).  See profiles/.
+# Newton work: A + B * (Newton updates per cell) [+ C * (share of solves with a single-
+# precision start)].  See profiles/.
 FP64_FLOPS_MODEL = {
     # the 128^3 box at rms Ma 0.8 (3.97 updates per cell: 10509 flops per cell) and 0.3
     # (3.21: 8619)
     "fp64": (691.0, 2472.0),
-    "mixed": (542.0, 1051.0),
+    # the precision form (single-precision start, then FP32-direction Newton steps): its
+    # per-cell part and per-update cost from the form without the start (3.99 updates per
+    # cell: 4722 flops per cell), and C, the full FP64 evaluation that a solve after a start
+    # takes in place of the cached one, from the 128^3 box at rms Ma 0.8 (2.003 updates, every
+    # solve started: 3401) and 0.3 (1.982: 3375)
+    "mixed": (542.0, 1051.0, 752.0),
     # the nine-constraint (z-mirror) solve of lattices one cell thick in z: the 2048x1024
     # airfoil at 0.018 updates per cell (686 flops per cell) and the quasi-2-D 2048x1024 box
     # at 3.26 (5129)
     "fp64_2d": (661.0, 1369.0),
     # FP64 storage with the single-precision Newton direction (root finder 2): the FP64 path's
     # per-cell part and the 128^3 box's count (4869 flops per cell at 3.99 updates per cell)
-    "fp64_fp32dir": (691.0, 1047.0)}
+    "fp64_fp32dir": (691.0, 1047.0),
+    # root finder 3 (2 after a single-precision start): as root finder 2, with C from the
+    # 128^3 box at rms Ma 0.8 (2.003 updates, every solve started: 3552 flops per cell) and
+    # 0.3 (1.982: 3526)
+    "fp64_fp32start": (691.0, 1047.0, 761.0)}
 # DRAM bytes (read + write) per launch of the step kernel from ncu, per workload and
 # precision, with the hash of the step kernel's code they were captured with; reported as
 # null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are
@@ -557,7 +567,11 @@ def counter_shares(st0, st1, cell_steps: int) -> dict:
                 [round(h / cell_steps, 4) for h in hist[:4]] + [round(sum(hist[4:]) / cell_steps, 4)],
             "alpha_branch_share": [round((st1.eps_hist[k] - st0.eps_hist[k]) / cell_steps, 4)
                                    for k in range(4)],
-            "fallback_share": round((st1.failed_cells - st0.failed_cells) / cell_steps, 6)}
+            "fallback_share": round((st1.failed_cells - st0.failed_cells) / cell_steps, 6),
+            "start32_steps_per_cell": round((st1.start32_updates - st0.start32_updates)
+                                            / cell_steps, 4),
+            "start32_solve_share": round((st1.start32_solves - st0.start32_solves)
+                                         / cell_steps, 4)}
 
 
 def l1_rel(a, b, fl):
@@ -646,7 +660,8 @@ def root_finder_section(args, local, s, newton_mlups: float):
     ref = None
     fl = s.mask == 0
     for name, over in (("newton", {}), ("chord", {"root_finder": 1}),
-                       ("fp32dir", {"root_finder": 2}), ("newton_tol_1e-10", {"newton_tol": 1e-10}),
+                       ("fp32dir", {"root_finder": 2}), ("fp32start", {"root_finder": 3}),
+                       ("newton_tol_1e-10", {"newton_tol": 1e-10}),
                        ("newton_tol_1e-8", {"newton_tol": 1e-8})):
         L = Lattice.from_setup(s, precision=C.LBM39_FP64, device=f"cuda:{local}", **over)
         c0 = L.stats().conserved
@@ -667,6 +682,10 @@ def root_finder_section(args, local, s, newton_mlups: float):
         out[name] = {"mlups": round(s.ncells * args.steps / (ms * 1e-3) / 1e6, 3),
                      "newton_updates_per_cell": round((st1.newton_updates - st0.newton_updates)
                                                       / (int(fl.sum()) * args.steps), 4),
+                     **({"start32_steps_per_cell":
+                         round((st1.start32_updates - st0.start32_updates)
+                               / (int(fl.sum()) * args.steps), 4)}
+                        if name == "fp32start" else {}),
                      "max_rel_diff_vs_newton_rho_u_T": [float("%.2e" % v) for v in d],
                      "conservation_drift_rel": [float("%.2e" % v)
                                                 for v in drift_rel(c0, st1.conserved)]}
@@ -732,9 +751,11 @@ def main():
                     help="arrival rate (Hz) of the serving section: saturating by default")
     ap.add_argument("--developed-at", type=int, default=3000,
                     help="airfoil section: first step of the developed-flow window")
-    ap.add_argument("--root-finder", default="newton", choices=["newton", "chord", "fp32dir"],
+    ap.add_argument("--root-finder", default="newton",
+                    choices=["newton", "chord", "fp32dir", "fp32start"],
                     help="solver of the constraint equations (chord: the chord-Newton hybrid; "
-                         "fp32dir: Newton with a single-precision direction)")
+                         "fp32dir: Newton with a single-precision direction; fp32start: that "
+                         "after a single-precision start)")
     ap.add_argument("--start-at", type=int, default=0,
                     help="step the lattice to this time before the warm-up (developed flows)")
     ap.add_argument("--checkpoint-out", default=None,
@@ -779,7 +800,8 @@ def main():
 
     prec = C.LBM39_FP64 if args.precision == "fp64" else C.LBM39_MIXED
     s = make_setup(args.workload, args.mach)
-    solver = {"root_finder": {"newton": 0, "chord": 1, "fp32dir": 2}[args.root_finder],
+    solver = {"root_finder": {"newton": 0, "chord": 1, "fp32dir": 2,
+                              "fp32start": 3}[args.root_finder],
               "newton_tol": args.newton_tol}
     L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}", **solver)
     stream = L.stream
@@ -821,8 +843,10 @@ def main():
                and s.u_inf[2] == 0.0)
     model = FP64_FLOPS_MODEL.get(("fp64_2d" if reduced else args.precision)
                                  + ("" if args.root_finder == "newton" else "_" + args.root_finder))
-    achieved_tf = ((model[0] + model[1] * k_upd) * fluid / (step_ms * 1e-3) / 1e12
-                   if model else None)
+    flops_cell = (model[0] + model[1] * k_upd
+                  + (model[2] * shares["start32_solve_share"] if len(model) > 2 else 0.0)
+                  if model else None)
+    achieved_tf = flops_cell * fluid / (step_ms * 1e-3) / 1e12 if model else None
     hbm_gbs = BYTES_PER_UPDATE[args.precision] * fluid / (step_ms * 1e-3) / 1e9
     traffic = None
     if (NCU_TRAFFIC["kernel_hash"] == kernel_source_hash() and args.mach == 0.8
@@ -834,9 +858,11 @@ def main():
                 "traffic": round(traffic * 1e9) if traffic else None,
                 "peak_source": "FP64 FMA throughput measured in this run by lbm39_selftest_dfma "
                                "(of measured)",
-                "flops_per_cell_update": round(model[0] + model[1] * k_upd) if model else None,
-                "flops_model": (f"{model[0]:g} + {model[1]:g} x (Newton updates per cell), "
-                                "fitted to ncu FP64 instruction counts (2 per DFMA, 1 per "
+                "flops_per_cell_update": round(flops_cell) if model else None,
+                "flops_model": (f"{model[0]:g} + {model[1]:g} x (Newton updates per cell)"
+                                + (f" + {model[2]:g} x (share of solves with a single-"
+                                   "precision start)" if len(model) > 2 else "")
+                                + ", fitted to ncu FP64 instruction counts (2 per DFMA, 1 per "
                                 "DADD/DMUL)") if model else "none fitted for this solver",
                 "hbm": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": HBM_PEAK_GBS,
                         "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),

@@ -113,14 +113,19 @@ typedef struct {
                                least 1e-3 (a chord step), else forms J at the current
                                point; a chord step that does not reduce ||G||_2 is
                                replaced by a Newton step from the same point;
-                               2: Newton with a single-precision direction (the
-                               precision form's solver): the residual and the update
-                               in FP64, the Jacobian and its LDL^T in FP32, same
-                               stopping rule; each step contracts the residual by about
-                               cond(J) times the FP32 precision.
-                               1 and 2 converge to the same equilibrium as Newton (the
-                               residual that decides convergence is the FP64 one); FP64
-                               path with Pr = 1 only. */
+                               2: Newton with a single-precision direction: the
+                               residual and the update in FP64, the Jacobian and its
+                               LDL^T in FP32, same stopping rule; each step contracts
+                               the residual by about cond(J) times the FP32 precision;
+                               3: 2 after a single-precision start (the precision
+                               form's solver): from the cached equilibrium rounded to
+                               FP32, Newton steps entirely in FP32 while the FP32
+                               residual max|G| is at least 1e-4 (at most 4, each kept
+                               only if it lowers max|G|), then 2 from there.
+                               1, 2 and 3 converge to the same equilibrium as Newton
+                               (the residual that decides convergence is the FP64 one);
+                               FP64 path with Pr = 1 only (the precision form always
+                               uses 3). */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;
@@ -135,6 +140,10 @@ typedef struct {
   int64_t eps_hist[4];      /* cell-steps by alpha branch of Eq. alpha */
   double conserved[5];      /* sums over fluid cells of rho, rho u_x, rho u_y,
                                rho u_z, rho E = (sum f|xi|^2 + sum g)/2 */
+  int64_t start32_updates;  /* float steps of single-precision starts (root_finder 3
+                               and the precision form), summed over cells and steps;
+                               not among newton_updates */
+  int64_t start32_solves;   /* cell-steps whose solve kept at least one of them */
 } lbm39_stats_t;
 
 /* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice

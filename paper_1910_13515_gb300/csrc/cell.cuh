@@ -175,12 +175,12 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
   for (int k = 0; k < S::N; ++k) G[k] = s[k] - m[S::idx(k)];
 }
 
-template <int N>
-__device__ __forceinline__ double max_abs(const double (&v)[N]) {
-  double r = 0.0;
+template <class T, int N>
+__device__ __forceinline__ T max_abs(const T (&v)[N]) {
+  T r = T(0);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    const double a = fabs(v[k]);
+    const T a = fabs(v[k]);
     r = (a <= r) ? r : a;  // NaN propagates
   }
   return r;
@@ -196,62 +196,34 @@ __device__ __forceinline__ double sum_sq(const double (&v)[N]) {
 
 // In-place LDL^T of a packed symmetric N x N J: unit-lower L below a diagonal
 // D, with rd the reciprocals of D's entries.  False if a pivot is not positive
-// (J not numerically SPD).  FP64: right-looking elimination -- pivot k scales
-// its column once (L_ik = a_ik / d_k) and updates the trailing matrix with
-// a_ij -= L_ik a_jk, so each multiplier is one product and every other
-// operation a fused multiply-add (the FP64 pipe bounds the step).  FP32 (the
-// precision form's direction): left-looking, with v_k = L_jk d_k formed per
-// column, which keeps fewer values live.
+// (J not numerically SPD).  Right-looking elimination: pivot k scales its column
+// once (L_ik = a_ik / d_k) and updates the trailing matrix with a_ij -= L_ik a_jk,
+// so each multiplier is one product and every other operation a fused
+// multiply-add (in FP64 the FP64 pipe bounds the step), and the updates of a
+// column are independent of one another (short dependency chains for the FP32
+// factorisations of the single-precision direction).
 template <class T, int N = NM>
 __device__ __forceinline__ bool ldlt_factor(T (&J)[N * (N + 1) / 2], T (&rd)[N]) {
   bool ok = true;
-  if constexpr (sizeof(T) == 8) {
-    static_for<0, N>([&](auto KK) {
-      constexpr int k = decltype(KK)::value;
-      const T dk = J[tri(k, k)];
-      ok = ok && (dk > T(0));
-      rd[k] = recip(dk);
-      T w[N];  // column k below the pivot, unscaled
-      static_for<k + 1, N>([&](auto II) {
-        constexpr int i = decltype(II)::value;
-        w[i] = J[tri(i, k)];
-        J[tri(i, k)] = w[i] * rd[k];
-      });
-      static_for<k + 1, N>([&](auto II) {
-        constexpr int i = decltype(II)::value;
-        static_for<k + 1, i + 1>([&](auto JJ) {
-          constexpr int j = decltype(JJ)::value;
-          J[tri(i, j)] = fma(-J[tri(i, k)], w[j], J[tri(i, j)]);
-        });
+  static_for<0, N>([&](auto KK) {
+    constexpr int k = decltype(KK)::value;
+    const T dk = J[tri(k, k)];
+    ok = ok && (dk > T(0));
+    rd[k] = recip(dk);
+    T w[N];  // column k below the pivot, unscaled
+    static_for<k + 1, N>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      w[i] = J[tri(i, k)];
+      J[tri(i, k)] = w[i] * rd[k];
+    });
+    static_for<k + 1, N>([&](auto II) {
+      constexpr int i = decltype(II)::value;
+      static_for<k + 1, i + 1>([&](auto JJ) {
+        constexpr int j = decltype(JJ)::value;
+        J[tri(i, j)] = fma(-J[tri(i, k)], w[j], J[tri(i, j)]);
       });
     });
-  } else {
-    static_for<0, N>([&](auto JJ) {
-      constexpr int j = decltype(JJ)::value;
-      T v[N];
-      static_for<0, j>([&](auto K) {
-        constexpr int k = decltype(K)::value;
-        v[k] = J[tri(j, k)] * J[tri(k, k)];
-      });
-      T dj = J[tri(j, j)];
-      static_for<0, j>([&](auto K) {
-        constexpr int k = decltype(K)::value;
-        dj = fma(-J[tri(j, k)], v[k], dj);
-      });
-      ok = ok && (dj > T(0));
-      J[tri(j, j)] = dj;
-      rd[j] = recip(dj);
-      static_for<j + 1, N>([&](auto II) {
-        constexpr int i = decltype(II)::value;
-        T a = J[tri(i, j)];
-        static_for<0, j>([&](auto K) {
-          constexpr int k = decltype(K)::value;
-          a = fma(-J[tri(i, k)], v[k], a);
-        });
-        J[tri(i, j)] = a * rd[j];
-      });
-    });
-  }
+  });
   return ok;
 }
 
@@ -330,9 +302,31 @@ __device__ __forceinline__ bool ldlt_solve(T (&J)[N * (N + 1) / 2], T (&b)[N]) {
   return ok;
 }
 
+// Single-precision direction (the precision form's Newton steps and the
+// single-precision start): J = sum_i F_i phi phi^T from the float equilibrium
+// at Fp (Q values), J d = b by the float LDL^T, b at bp (the system's N values,
+// overwritten by d).  False if a pivot is not positive.  Not inlined: its one
+// copy serves both callers, which keeps the step kernel's code (and its
+// instruction-cache footprint) small; the arrays pass through the stack.
+template <bool D2>
+__device__ __noinline__ bool dir32(const float* __restrict__ Fp, float* __restrict__ bp) {
+  constexpr int N = Sys<D2>::N;
+  float Ff[Q], J[N * (N + 1) / 2], s[N], b[N];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Ff[i] = Fp[i];
+  if constexpr (D2) gen::moments2d<float>(Ff, s, J);
+  else gen::moments<float>(Ff, s, J);
+#pragma unroll
+  for (int k = 0; k < N; ++k) b[k] = bp[k];
+  const bool ok = ldlt_solve<float, N>(J, b);
+#pragma unroll
+  for (int k = 0; k < N; ++k) bp[k] = b[k];
+  return ok;
+}
+
 // Newton direction: J = sum_i F_i phi phi^T (Sec. 5 step table), J delta = b,
 // b and delta in dl.  FP64 path: J and LDL^T in FP64.  Precision form: in
-// FP32 (the residual and the update stay FP64, so the iteration still
+// FP32 (dir32; the residual and the update stay FP64, so the iteration still
 // converges to the FP64 root).
 template <int BLK, bool MIXED, bool D2 = false>
 __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
@@ -366,14 +360,12 @@ __device__ __forceinline__ bool newton_direction(WS<BLK> F, WS<BLK> dl) {
     for (int k = 0; k < N; ++k) dl[k] = b[k];
     return ok;
   } else {
-    float Ff[Q], J[N * (N + 1) / 2], s[N], bf[N];
+    float Ff[Q], bf[N];
 #pragma unroll
     for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
-    if constexpr (D2) gen::moments2d<float>(Ff, s, J);
-    else gen::moments<float>(Ff, s, J);
 #pragma unroll
     for (int k = 0; k < N; ++k) bf[k] = trunc_float(dl[k]);
-    const bool ok = ldlt_solve<float, N>(J, bf);
+    const bool ok = dir32<D2>(Ff, bf);
 #pragma unroll
     for (int k = 0; k < N; ++k) dl[k] = (double)bf[k];
     return ok;
@@ -439,6 +431,78 @@ __device__ NewtonResult newton(WS<BLK> w, const Phys& ph, int maxit, bool cached
     ls = 0;
   }
   return NewtonResult{n, failed};
+}
+
+// Single-precision start of a solve (root finder 3, and the precision form's
+// solver).  From a warm start the first Newton steps need the residual only to a
+// few digits, and float arithmetic issues at 64 times the FP64 rate here.  From
+// F~ = F in float (F: the cached exp(Phi lam)), Newton steps in float: the float
+// residual G of F~ (the generated sums), J d = G (dir32), and the trial
+// equilibrium F~_i exp(-phi(xi_i) . d) with its residual; while max|G| >=
+// START32_THETA, at most START32_MAXIT times, and a step is kept only if it lowers
+// max|G| (else the phase ends).  Then lam -= (the sum of the kept d) in FP64, and
+// the FP64-residual Newton finishes the solve from there, so the equilibrium is
+// the one every root finder reaches.  Returns the number of steps kept (0: lam
+// and the cached F untouched).
+constexpr float START32_THETA = 1e-4f;
+constexpr int START32_MAXIT = 4;
+
+template <int BLK, bool D2 = false>
+__device__ __forceinline__ int start32(WS<BLK> w) {
+  using S = Sys<D2>;
+  constexpr int N = S::N;
+  WS<BLK> lam = w.at(WS_LAM), F = w.at(WS_E), m = w.at(WS_M);
+  float Ff[Q], G[N], dsum[N];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Ff[i] = trunc_float(F[i]);
+  {
+    float s[N];
+    if constexpr (D2) gen::moments_s2d<float>(Ff, s);
+    else gen::moments_s<float>(Ff, s);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      G[k] = s[k] - trunc_float(m[S::idx(k)]);
+      dsum[k] = 0.0f;
+    }
+  }
+  float r = max_abs(G);
+  int n = 0;
+  while (n < START32_MAXIT && r >= START32_THETA) {  // false for a NaN residual
+    float d[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) d[k] = G[k];
+    if (!dir32<D2>(Ff, d)) break;
+    float l[NM], x[Q];  // -d at the system's places of the 13, and its exponents
+#pragma unroll
+    for (int k = 0; k < NM; ++k) l[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) l[S::idx(k)] = -d[k];
+    if constexpr (D2) gen::exponents2d<float>(l, x);
+    else gen::exponents<float>(l, x);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) x[i] = Ff[i] * expf(x[i]);
+    float s[N];
+    if constexpr (D2) gen::moments_s2d<float>(x, s);
+    else gen::moments_s<float>(x, s);
+#pragma unroll
+    for (int k = 0; k < N; ++k) s[k] -= trunc_float(m[S::idx(k)]);
+    const float rt = max_abs(s);
+    if (!(rt < r)) break;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Ff[i] = x[i];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      G[k] = s[k];
+      dsum[k] += d[k];
+    }
+    r = rt;
+    ++n;
+  }
+  if (n > 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) lam[S::idx(k)] -= (double)dsum[k];
+  }
+  return n;
 }
 
 // Chord-Newton hybrid for the same equations (a second root finder; the

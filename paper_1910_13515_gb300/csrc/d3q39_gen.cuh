@@ -8,97 +8,99 @@ namespace gen {
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
-// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium).
-__device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]) {
-  const double c0_0 = l[0];
+// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium),
+// in the type of l (double; float for the single-precision start of a solve).
+template <class T>
+__device__ __forceinline__ void exponents(const T (&l)[13], T (&e)[39]) {
+  const T c0_0 = l[0];
   e[0] = c0_0;
-  const double c1_0 = l[0] + l[6];
-  const double c1_z = l[3] + l[12];
-  const double t1_0_0 = c1_0 + c1_z;
-  const double t1_0_1 = c1_0 - c1_z;
+  const T c1_0 = l[0] + l[6];
+  const T c1_z = l[3] + l[12];
+  const T t1_0_0 = c1_0 + c1_z;
+  const T t1_0_1 = c1_0 - c1_z;
   e[5] = t1_0_0;
   e[6] = t1_0_1;
-  const double c2_0 = fma(double(4), l[6], l[0]);
-  const double c2_z = fma(double(8), l[12], mul_rn(double(2), l[3]));
-  const double t2_0_0 = c2_0 + c2_z;
-  const double t2_0_1 = c2_0 - c2_z;
+  const T c2_0 = fma(T(4), l[6], l[0]);
+  const T c2_z = fma(T(8), l[12], mul_rn(T(2), l[3]));
+  const T t2_0_0 = c2_0 + c2_z;
+  const T t2_0_1 = c2_0 - c2_z;
   e[19] = t2_0_0;
   e[20] = t2_0_1;
-  const double c3_0 = fma(double(9), l[6], l[0]);
-  const double c3_z = fma(double(27), l[12], mul_rn(double(3), l[3]));
-  const double t3_0_0 = c3_0 + c3_z;
-  const double t3_0_1 = c3_0 - c3_z;
+  const T c3_0 = fma(T(9), l[6], l[0]);
+  const T c3_z = fma(T(27), l[12], mul_rn(T(3), l[3]));
+  const T t3_0_0 = c3_0 + c3_z;
+  const T t3_0_1 = c3_0 - c3_z;
   e[37] = t3_0_0;
   e[38] = t3_0_1;
-  const double c4_0 = l[0] + l[5];
-  const double c4_y = l[2] + l[11];
-  const double t4_0_0 = c4_0 + c4_y;
-  const double t4_0_1 = c4_0 - c4_y;
+  const T c4_0 = l[0] + l[5];
+  const T c4_y = l[2] + l[11];
+  const T t4_0_0 = c4_0 + c4_y;
+  const T t4_0_1 = c4_0 - c4_y;
   e[3] = t4_0_0;
   e[4] = t4_0_1;
-  const double c5_0 = fma(double(4), l[5], l[0]);
-  const double c5_y = fma(double(8), l[11], mul_rn(double(2), l[2]));
-  const double t5_0_0 = c5_0 + c5_y;
-  const double t5_0_1 = c5_0 - c5_y;
+  const T c5_0 = fma(T(4), l[5], l[0]);
+  const T c5_y = fma(T(8), l[11], mul_rn(T(2), l[2]));
+  const T t5_0_0 = c5_0 + c5_y;
+  const T t5_0_1 = c5_0 - c5_y;
   e[17] = t5_0_0;
   e[18] = t5_0_1;
-  const double c6_0 = fma(double(4), l[6], fma(double(4), l[5], l[0]));
-  const double c6_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
-  const double c6_z = fma(double(16), l[12], mul_rn(double(2), l[3]));
-  const double c6_yz = mul_rn(double(4), l[9]);
-  const double t6_0_0 = c6_0 + c6_y;
-  const double t6_0_1 = c6_0 - c6_y;
-  const double t6_0_2 = c6_z + c6_yz;
-  const double t6_0_3 = c6_z - c6_yz;
-  const double t6_1_0 = t6_0_0 + t6_0_2;
-  const double t6_1_1 = t6_0_0 - t6_0_2;
-  const double t6_1_2 = t6_0_1 + t6_0_3;
-  const double t6_1_3 = t6_0_1 - t6_0_3;
+  const T c6_0 = fma(T(4), l[6], fma(T(4), l[5], l[0]));
+  const T c6_y = fma(T(16), l[11], mul_rn(T(2), l[2]));
+  const T c6_z = fma(T(16), l[12], mul_rn(T(2), l[3]));
+  const T c6_yz = mul_rn(T(4), l[9]);
+  const T t6_0_0 = c6_0 + c6_y;
+  const T t6_0_1 = c6_0 - c6_y;
+  const T t6_0_2 = c6_z + c6_yz;
+  const T t6_0_3 = c6_z - c6_yz;
+  const T t6_1_0 = t6_0_0 + t6_0_2;
+  const T t6_1_1 = t6_0_0 - t6_0_2;
+  const T t6_1_2 = t6_0_1 + t6_0_3;
+  const T t6_1_3 = t6_0_1 - t6_0_3;
   e[29] = t6_1_0;
   e[31] = t6_1_1;
   e[32] = t6_1_2;
   e[30] = t6_1_3;
-  const double c7_0 = fma(double(9), l[5], l[0]);
-  const double c7_y = fma(double(27), l[11], mul_rn(double(3), l[2]));
-  const double t7_0_0 = c7_0 + c7_y;
-  const double t7_0_1 = c7_0 - c7_y;
+  const T c7_0 = fma(T(9), l[5], l[0]);
+  const T c7_y = fma(T(27), l[11], mul_rn(T(3), l[2]));
+  const T t7_0_0 = c7_0 + c7_y;
+  const T t7_0_1 = c7_0 - c7_y;
   e[35] = t7_0_0;
   e[36] = t7_0_1;
-  const double c8_0 = l[0] + l[4];
-  const double c8_x = l[1] + l[10];
-  const double t8_0_0 = c8_0 + c8_x;
-  const double t8_0_1 = c8_0 - c8_x;
+  const T c8_0 = l[0] + l[4];
+  const T c8_x = l[1] + l[10];
+  const T t8_0_0 = c8_0 + c8_x;
+  const T t8_0_1 = c8_0 - c8_x;
   e[1] = t8_0_0;
   e[2] = t8_0_1;
-  const double c9_0 = l[0] + l[4] + l[5] + l[6];
-  const double c9_x = fma(double(3), l[10], l[1]);
-  const double c9_y = fma(double(3), l[11], l[2]);
-  const double c9_z = fma(double(3), l[12], l[3]);
-  const double c9_xy = l[7];
-  const double c9_xz = l[8];
-  const double c9_yz = l[9];
-  const double t9_0_0 = c9_0 + c9_x;
-  const double t9_0_1 = c9_0 - c9_x;
-  const double t9_0_2 = c9_y + c9_xy;
-  const double t9_0_3 = c9_y - c9_xy;
-  const double t9_0_4 = c9_z + c9_xz;
-  const double t9_0_5 = c9_z - c9_xz;
-  const double t9_1_0 = t9_0_0 + t9_0_2;
-  const double t9_1_1 = t9_0_0 - t9_0_2;
-  const double t9_1_2 = t9_0_1 + t9_0_3;
-  const double t9_1_3 = t9_0_1 - t9_0_3;
-  const double t9_1_4 = t9_0_4 + c9_yz;
-  const double t9_1_5 = t9_0_4 - c9_yz;
-  const double t9_1_6 = t9_0_5 + c9_yz;
-  const double t9_1_7 = t9_0_5 - c9_yz;
-  const double t9_2_0 = t9_1_0 + t9_1_4;
-  const double t9_2_1 = t9_1_0 - t9_1_4;
-  const double t9_2_2 = t9_1_1 + t9_1_5;
-  const double t9_2_3 = t9_1_1 - t9_1_5;
-  const double t9_2_4 = t9_1_2 + t9_1_6;
-  const double t9_2_5 = t9_1_2 - t9_1_6;
-  const double t9_2_6 = t9_1_3 + t9_1_7;
-  const double t9_2_7 = t9_1_3 - t9_1_7;
+  const T c9_0 = l[0] + l[4] + l[5] + l[6];
+  const T c9_x = fma(T(3), l[10], l[1]);
+  const T c9_y = fma(T(3), l[11], l[2]);
+  const T c9_z = fma(T(3), l[12], l[3]);
+  const T c9_xy = l[7];
+  const T c9_xz = l[8];
+  const T c9_yz = l[9];
+  const T t9_0_0 = c9_0 + c9_x;
+  const T t9_0_1 = c9_0 - c9_x;
+  const T t9_0_2 = c9_y + c9_xy;
+  const T t9_0_3 = c9_y - c9_xy;
+  const T t9_0_4 = c9_z + c9_xz;
+  const T t9_0_5 = c9_z - c9_xz;
+  const T t9_1_0 = t9_0_0 + t9_0_2;
+  const T t9_1_1 = t9_0_0 - t9_0_2;
+  const T t9_1_2 = t9_0_1 + t9_0_3;
+  const T t9_1_3 = t9_0_1 - t9_0_3;
+  const T t9_1_4 = t9_0_4 + c9_yz;
+  const T t9_1_5 = t9_0_4 - c9_yz;
+  const T t9_1_6 = t9_0_5 + c9_yz;
+  const T t9_1_7 = t9_0_5 - c9_yz;
+  const T t9_2_0 = t9_1_0 + t9_1_4;
+  const T t9_2_1 = t9_1_0 - t9_1_4;
+  const T t9_2_2 = t9_1_1 + t9_1_5;
+  const T t9_2_3 = t9_1_1 - t9_1_5;
+  const T t9_2_4 = t9_1_2 + t9_1_6;
+  const T t9_2_5 = t9_1_2 - t9_1_6;
+  const T t9_2_6 = t9_1_3 + t9_1_7;
+  const T t9_2_7 = t9_1_3 - t9_1_7;
   e[7] = t9_2_0;
   e[9] = t9_2_1;
   e[11] = t9_2_2;
@@ -107,109 +109,110 @@ __device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]
   e[12] = t9_2_5;
   e[10] = t9_2_6;
   e[8] = t9_2_7;
-  const double c10_0 = fma(double(4), l[4], l[0]);
-  const double c10_x = fma(double(8), l[10], mul_rn(double(2), l[1]));
-  const double t10_0_0 = c10_0 + c10_x;
-  const double t10_0_1 = c10_0 - c10_x;
+  const T c10_0 = fma(T(4), l[4], l[0]);
+  const T c10_x = fma(T(8), l[10], mul_rn(T(2), l[1]));
+  const T t10_0_0 = c10_0 + c10_x;
+  const T t10_0_1 = c10_0 - c10_x;
   e[15] = t10_0_0;
   e[16] = t10_0_1;
-  const double c11_0 = fma(double(4), l[6], fma(double(4), l[4], l[0]));
-  const double c11_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
-  const double c11_z = fma(double(16), l[12], mul_rn(double(2), l[3]));
-  const double c11_xz = mul_rn(double(4), l[8]);
-  const double t11_0_0 = c11_0 + c11_x;
-  const double t11_0_1 = c11_0 - c11_x;
-  const double t11_0_2 = c11_z + c11_xz;
-  const double t11_0_3 = c11_z - c11_xz;
-  const double t11_1_0 = t11_0_0 + t11_0_2;
-  const double t11_1_1 = t11_0_0 - t11_0_2;
-  const double t11_1_2 = t11_0_1 + t11_0_3;
-  const double t11_1_3 = t11_0_1 - t11_0_3;
+  const T c11_0 = fma(T(4), l[6], fma(T(4), l[4], l[0]));
+  const T c11_x = fma(T(16), l[10], mul_rn(T(2), l[1]));
+  const T c11_z = fma(T(16), l[12], mul_rn(T(2), l[3]));
+  const T c11_xz = mul_rn(T(4), l[8]);
+  const T t11_0_0 = c11_0 + c11_x;
+  const T t11_0_1 = c11_0 - c11_x;
+  const T t11_0_2 = c11_z + c11_xz;
+  const T t11_0_3 = c11_z - c11_xz;
+  const T t11_1_0 = t11_0_0 + t11_0_2;
+  const T t11_1_1 = t11_0_0 - t11_0_2;
+  const T t11_1_2 = t11_0_1 + t11_0_3;
+  const T t11_1_3 = t11_0_1 - t11_0_3;
   e[25] = t11_1_0;
   e[27] = t11_1_1;
   e[28] = t11_1_2;
   e[26] = t11_1_3;
-  const double c12_0 = fma(double(4), l[5], fma(double(4), l[4], l[0]));
-  const double c12_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
-  const double c12_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
-  const double c12_xy = mul_rn(double(4), l[7]);
-  const double t12_0_0 = c12_0 + c12_x;
-  const double t12_0_1 = c12_0 - c12_x;
-  const double t12_0_2 = c12_y + c12_xy;
-  const double t12_0_3 = c12_y - c12_xy;
-  const double t12_1_0 = t12_0_0 + t12_0_2;
-  const double t12_1_1 = t12_0_0 - t12_0_2;
-  const double t12_1_2 = t12_0_1 + t12_0_3;
-  const double t12_1_3 = t12_0_1 - t12_0_3;
+  const T c12_0 = fma(T(4), l[5], fma(T(4), l[4], l[0]));
+  const T c12_x = fma(T(16), l[10], mul_rn(T(2), l[1]));
+  const T c12_y = fma(T(16), l[11], mul_rn(T(2), l[2]));
+  const T c12_xy = mul_rn(T(4), l[7]);
+  const T t12_0_0 = c12_0 + c12_x;
+  const T t12_0_1 = c12_0 - c12_x;
+  const T t12_0_2 = c12_y + c12_xy;
+  const T t12_0_3 = c12_y - c12_xy;
+  const T t12_1_0 = t12_0_0 + t12_0_2;
+  const T t12_1_1 = t12_0_0 - t12_0_2;
+  const T t12_1_2 = t12_0_1 + t12_0_3;
+  const T t12_1_3 = t12_0_1 - t12_0_3;
   e[21] = t12_1_0;
   e[23] = t12_1_1;
   e[24] = t12_1_2;
   e[22] = t12_1_3;
-  const double c13_0 = fma(double(9), l[4], l[0]);
-  const double c13_x = fma(double(27), l[10], mul_rn(double(3), l[1]));
-  const double t13_0_0 = c13_0 + c13_x;
-  const double t13_0_1 = c13_0 - c13_x;
+  const T c13_0 = fma(T(9), l[4], l[0]);
+  const T c13_x = fma(T(27), l[10], mul_rn(T(3), l[1]));
+  const T t13_0_0 = c13_0 + c13_x;
+  const T t13_0_1 = c13_0 - c13_x;
   e[33] = t13_0_0;
   e[34] = t13_0_1;
 }
 
 // The same with the z-odd multipliers zero (lattice one cell thick in z, u_z = 0).
-__device__ __forceinline__ void exponents2d(const double (&l)[13], double (&e)[39]) {
-  const double c0_0 = l[0];
+template <class T>
+__device__ __forceinline__ void exponents2d(const T (&l)[13], T (&e)[39]) {
+  const T c0_0 = l[0];
   e[0] = c0_0;
-  const double c1_0 = l[0] + l[6];
+  const T c1_0 = l[0] + l[6];
   e[5] = c1_0;
   e[6] = c1_0;
-  const double c2_0 = fma(double(4), l[6], l[0]);
+  const T c2_0 = fma(T(4), l[6], l[0]);
   e[19] = c2_0;
   e[20] = c2_0;
-  const double c3_0 = fma(double(9), l[6], l[0]);
+  const T c3_0 = fma(T(9), l[6], l[0]);
   e[37] = c3_0;
   e[38] = c3_0;
-  const double c4_0 = l[0] + l[5];
-  const double c4_y = l[2] + l[11];
-  const double t4_0_0 = c4_0 + c4_y;
-  const double t4_0_1 = c4_0 - c4_y;
+  const T c4_0 = l[0] + l[5];
+  const T c4_y = l[2] + l[11];
+  const T t4_0_0 = c4_0 + c4_y;
+  const T t4_0_1 = c4_0 - c4_y;
   e[3] = t4_0_0;
   e[4] = t4_0_1;
-  const double c5_0 = fma(double(4), l[5], l[0]);
-  const double c5_y = fma(double(8), l[11], mul_rn(double(2), l[2]));
-  const double t5_0_0 = c5_0 + c5_y;
-  const double t5_0_1 = c5_0 - c5_y;
+  const T c5_0 = fma(T(4), l[5], l[0]);
+  const T c5_y = fma(T(8), l[11], mul_rn(T(2), l[2]));
+  const T t5_0_0 = c5_0 + c5_y;
+  const T t5_0_1 = c5_0 - c5_y;
   e[17] = t5_0_0;
   e[18] = t5_0_1;
-  const double c6_0 = fma(double(4), l[6], fma(double(4), l[5], l[0]));
-  const double c6_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
-  const double t6_0_0 = c6_0 + c6_y;
-  const double t6_0_1 = c6_0 - c6_y;
+  const T c6_0 = fma(T(4), l[6], fma(T(4), l[5], l[0]));
+  const T c6_y = fma(T(16), l[11], mul_rn(T(2), l[2]));
+  const T t6_0_0 = c6_0 + c6_y;
+  const T t6_0_1 = c6_0 - c6_y;
   e[29] = t6_0_0;
   e[31] = t6_0_0;
   e[32] = t6_0_1;
   e[30] = t6_0_1;
-  const double c7_0 = fma(double(9), l[5], l[0]);
-  const double c7_y = fma(double(27), l[11], mul_rn(double(3), l[2]));
-  const double t7_0_0 = c7_0 + c7_y;
-  const double t7_0_1 = c7_0 - c7_y;
+  const T c7_0 = fma(T(9), l[5], l[0]);
+  const T c7_y = fma(T(27), l[11], mul_rn(T(3), l[2]));
+  const T t7_0_0 = c7_0 + c7_y;
+  const T t7_0_1 = c7_0 - c7_y;
   e[35] = t7_0_0;
   e[36] = t7_0_1;
-  const double c8_0 = l[0] + l[4];
-  const double c8_x = l[1] + l[10];
-  const double t8_0_0 = c8_0 + c8_x;
-  const double t8_0_1 = c8_0 - c8_x;
+  const T c8_0 = l[0] + l[4];
+  const T c8_x = l[1] + l[10];
+  const T t8_0_0 = c8_0 + c8_x;
+  const T t8_0_1 = c8_0 - c8_x;
   e[1] = t8_0_0;
   e[2] = t8_0_1;
-  const double c9_0 = l[0] + l[4] + l[5] + l[6];
-  const double c9_x = fma(double(3), l[10], l[1]);
-  const double c9_y = fma(double(3), l[11], l[2]);
-  const double c9_xy = l[7];
-  const double t9_0_0 = c9_0 + c9_x;
-  const double t9_0_1 = c9_0 - c9_x;
-  const double t9_0_2 = c9_y + c9_xy;
-  const double t9_0_3 = c9_y - c9_xy;
-  const double t9_1_0 = t9_0_0 + t9_0_2;
-  const double t9_1_1 = t9_0_0 - t9_0_2;
-  const double t9_1_2 = t9_0_1 + t9_0_3;
-  const double t9_1_3 = t9_0_1 - t9_0_3;
+  const T c9_0 = l[0] + l[4] + l[5] + l[6];
+  const T c9_x = fma(T(3), l[10], l[1]);
+  const T c9_y = fma(T(3), l[11], l[2]);
+  const T c9_xy = l[7];
+  const T t9_0_0 = c9_0 + c9_x;
+  const T t9_0_1 = c9_0 - c9_x;
+  const T t9_0_2 = c9_y + c9_xy;
+  const T t9_0_3 = c9_y - c9_xy;
+  const T t9_1_0 = t9_0_0 + t9_0_2;
+  const T t9_1_1 = t9_0_0 - t9_0_2;
+  const T t9_1_2 = t9_0_1 + t9_0_3;
+  const T t9_1_3 = t9_0_1 - t9_0_3;
   e[7] = t9_1_0;
   e[9] = t9_1_0;
   e[11] = t9_1_1;
@@ -218,40 +221,40 @@ __device__ __forceinline__ void exponents2d(const double (&l)[13], double (&e)[3
   e[12] = t9_1_2;
   e[10] = t9_1_3;
   e[8] = t9_1_3;
-  const double c10_0 = fma(double(4), l[4], l[0]);
-  const double c10_x = fma(double(8), l[10], mul_rn(double(2), l[1]));
-  const double t10_0_0 = c10_0 + c10_x;
-  const double t10_0_1 = c10_0 - c10_x;
+  const T c10_0 = fma(T(4), l[4], l[0]);
+  const T c10_x = fma(T(8), l[10], mul_rn(T(2), l[1]));
+  const T t10_0_0 = c10_0 + c10_x;
+  const T t10_0_1 = c10_0 - c10_x;
   e[15] = t10_0_0;
   e[16] = t10_0_1;
-  const double c11_0 = fma(double(4), l[6], fma(double(4), l[4], l[0]));
-  const double c11_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
-  const double t11_0_0 = c11_0 + c11_x;
-  const double t11_0_1 = c11_0 - c11_x;
+  const T c11_0 = fma(T(4), l[6], fma(T(4), l[4], l[0]));
+  const T c11_x = fma(T(16), l[10], mul_rn(T(2), l[1]));
+  const T t11_0_0 = c11_0 + c11_x;
+  const T t11_0_1 = c11_0 - c11_x;
   e[25] = t11_0_0;
   e[27] = t11_0_0;
   e[28] = t11_0_1;
   e[26] = t11_0_1;
-  const double c12_0 = fma(double(4), l[5], fma(double(4), l[4], l[0]));
-  const double c12_x = fma(double(16), l[10], mul_rn(double(2), l[1]));
-  const double c12_y = fma(double(16), l[11], mul_rn(double(2), l[2]));
-  const double c12_xy = mul_rn(double(4), l[7]);
-  const double t12_0_0 = c12_0 + c12_x;
-  const double t12_0_1 = c12_0 - c12_x;
-  const double t12_0_2 = c12_y + c12_xy;
-  const double t12_0_3 = c12_y - c12_xy;
-  const double t12_1_0 = t12_0_0 + t12_0_2;
-  const double t12_1_1 = t12_0_0 - t12_0_2;
-  const double t12_1_2 = t12_0_1 + t12_0_3;
-  const double t12_1_3 = t12_0_1 - t12_0_3;
+  const T c12_0 = fma(T(4), l[5], fma(T(4), l[4], l[0]));
+  const T c12_x = fma(T(16), l[10], mul_rn(T(2), l[1]));
+  const T c12_y = fma(T(16), l[11], mul_rn(T(2), l[2]));
+  const T c12_xy = mul_rn(T(4), l[7]);
+  const T t12_0_0 = c12_0 + c12_x;
+  const T t12_0_1 = c12_0 - c12_x;
+  const T t12_0_2 = c12_y + c12_xy;
+  const T t12_0_3 = c12_y - c12_xy;
+  const T t12_1_0 = t12_0_0 + t12_0_2;
+  const T t12_1_1 = t12_0_0 - t12_0_2;
+  const T t12_1_2 = t12_0_1 + t12_0_3;
+  const T t12_1_3 = t12_0_1 - t12_0_3;
   e[21] = t12_1_0;
   e[23] = t12_1_1;
   e[24] = t12_1_2;
   e[22] = t12_1_3;
-  const double c13_0 = fma(double(9), l[4], l[0]);
-  const double c13_x = fma(double(27), l[10], mul_rn(double(3), l[1]));
-  const double t13_0_0 = c13_0 + c13_x;
-  const double t13_0_1 = c13_0 - c13_x;
+  const T c13_0 = fma(T(9), l[4], l[0]);
+  const T c13_x = fma(T(27), l[10], mul_rn(T(3), l[1]));
+  const T t13_0_0 = c13_0 + c13_x;
+  const T t13_0_1 = c13_0 - c13_x;
   e[33] = t13_0_0;
   e[34] = t13_0_1;
 }

@@ -66,9 +66,8 @@ __global__ void __launch_bounds__(BLK) k_diag_fields(Desc d, int odd, double* ep
   load_solver_state<BLK>(d, cell, w);
   const bool marked = is_fallback_embedding<BLK>(lam);
   const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
-  NewtonResult nr;
-  if constexpr (SOLVER == 1) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
-  else nr = newton<BLK, (sizeof(P) == 4) || SOLVER == 2, D2>(w, d.ph, maxit, true);
+  int n32;
+  const NewtonResult nr = solve_cell<P, BLK, D2, SOLVER>(w, d.ph, maxit, n32);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   double f[Q];
   if (odd) gather_f<true, P>(d, cell, f);
@@ -103,6 +102,10 @@ extern "C" int lbm39_diag_fields(lbm39_lattice* L, double* eps, int32_t* n_upd) 
     k_diag_fields<double, true, 2><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
   else if (v.solver == 2)
     k_diag_fields<double, false, 2><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 3 && v.desc.d2)
+    k_diag_fields<double, true, 3><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
+  else if (v.solver == 3)
+    k_diag_fields<double, false, 3><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
   else if (v.desc.d2)
     k_diag_fields<double, true><<<grid, BLK, WS_BYTES, v.stream>>>(v.desc, odd, eps, n_upd);
   else

@@ -14,7 +14,7 @@ a, a monomial xi^p equals prod_a a^p * prod_{p_a odd} s_a, so
 This is the same arithmetic as the plain sums over 39 velocities, reorganised.
 
 Emitted:
-  exponents_fp64(l, e)        e_i = sum_k l_k phi_k(xi_i)         (Eq. discrete-equilibrium)
+  exponents<T>(l, e)          e_i = sum_k l_k phi_k(xi_i)         (Eq. discrete-equilibrium)
   moments<T>(F, s, J)         s_k = sum_i F_i phi_k,  J_kl = sum_i F_i phi_k phi_l (packed)
   f_moments(f, ...)           rho, j, sum f|xi|^2;  g_sum(g): sum g
   exp2_table                  2^(j/256), j = 0..255, correctly rounded (decimal arithmetic)
@@ -296,10 +296,13 @@ def gen_exponents(zsym=False):
     em = Emitter()
     if zsym:
         em("// The same with the z-odd multipliers zero (lattice one cell thick in z, u_z = 0).")
-        em("__device__ __forceinline__ void exponents2d(const double (&l)[13], double (&e)[39]) {")
+        em("template <class T>")
+        em("__device__ __forceinline__ void exponents2d(const T (&l)[13], T (&e)[39]) {")
     else:
-        em("// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium).")
-        em("__device__ __forceinline__ void exponents(const double (&l)[13], double (&e)[39]) {")
+        em("// e_i = sum_k l_k phi_k(xi_i) for every velocity (exponent of Eq. discrete-equilibrium),")
+        em("// in the type of l (double; float for the single-precision start of a solve).")
+        em("template <class T>")
+        em("__device__ __forceinline__ void exponents(const T (&l)[13], T (&e)[39]) {")
     for o, (key, axes, members) in enumerate(ORBITS):
         n = len(axes)
         # c_T = sum_k l_k * (coefficient of prod_{a in T} s_a in phi_k on this orbit)
@@ -328,7 +331,7 @@ def gen_exponents(zsym=False):
         for Tset, terms in cT.items():
             nm = "c%d_%s" % (o, "".join("xyz"[a] for a in Tset) or "0")
             if terms:
-                em(f"  const double {nm} = {lincomb(terms, 'double')};")
+                em(f"  const T {nm} = {lincomb(terms, 'T')};")
                 cname[Tset] = nm
             else:
                 cname[Tset] = None
@@ -359,13 +362,13 @@ def gen_exponents(zsym=False):
                     if expr == v or expr == vo:
                         nxt[key2] = expr
                     else:
-                        em(f"  const double {nm} = {expr};")
+                        em(f"  const T {nm} = {expr};")
                         nxt[key2] = nm
             cur = nxt
         for (sg, Tset), v in cur.items():
             assert Tset == ()
             i = members[sg]
-            em(f"  e[{i}] = {v if v is not None else '0.0'};")
+            em(f"  e[{i}] = {v if v is not None else 'T(0)'};")
     em("}")
     return em.lines
 

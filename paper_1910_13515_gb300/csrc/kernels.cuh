@@ -46,10 +46,14 @@ struct Desc {
   Phys ph;
 };
 
-enum { CTR_FAILED = 0, CTR_UPDATES = 1, CTR_HIST = 2, CTR_EPS = 34, CTR_N = 38 };
+// CTR_UPD32: float steps of single-precision starts; CTR_START32: solves that took one.
+enum {
+  CTR_FAILED = 0, CTR_UPDATES = 1, CTR_HIST = 2, CTR_EPS = 34, CTR_UPD32 = 38, CTR_START32 = 39,
+  CTR_N = 40
+};
 // Set by lbm39_init when some fluid cell starts with u_z != 0 (outside the
 // block counters: not reported by lbm39_stats).
-constexpr int CTR_ASYM = 40;
+constexpr int CTR_ASYM = 42;
 
 struct Coord {
   int x, y, z;
@@ -414,14 +418,35 @@ __device__ __forceinline__ int retry_budget(long long t) {
   return (t & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0;
 }
 
+// The constraint solve of a cell from the warm start in the workspace (F cached
+// at lam) with the lattice's root finder SOLVER (FP64 path): 0 Newton-Raphson;
+// 1 the chord-Newton hybrid (newton_chord); 2 Newton with a single-precision
+// direction (newton<BLK, true>); 3 that after a single-precision start
+// (start32).  The precision form (P = float) always takes 3.  n32: the float
+// steps of the start.
+template <class P, int BLK, bool D2, int SOLVER>
+__device__ __forceinline__ NewtonResult solve_cell(WS<BLK> w, const Phys& ph, int maxit,
+                                                   int& n32) {
+  n32 = 0;
+  if constexpr (SOLVER == 1 && sizeof(P) == 8) {
+    return newton_chord<BLK, D2>(w, ph, maxit, true);
+  } else {
+    bool cached = true;
+    if constexpr (sizeof(P) == 4 || SOLVER == 3) {
+      if (maxit > 0) {  // a cell on the fallback off a retry step takes no step at all
+        n32 = start32<BLK, D2>(w);
+        cached = n32 == 0;
+      }
+    }
+    return newton<BLK, sizeof(P) == 4 || SOLVER >= 2, D2>(w, ph, maxit, cached);
+  }
+}
+
 // One fluid cell's time step (even or odd AA pass): phases A, B and C, with
 // the Newton statistics added to the block's counters.  w: the cell's workspace.
 // D2: the nine-function constraint system of a z-mirror-symmetric lattice one
 // cell thick in z (Sys<true>; the same values as the full system).
-// SOLVER: the root finder of the constraint equations (FP64 path; the precision
-// form always uses 0): 0 Newton-Raphson; 1 the chord-Newton hybrid (newton_chord);
-// 2 Newton with a single-precision direction (newton<BLK, true>, the precision
-// form's solver).
+// SOLVER: the root finder of the constraint equations (solve_cell).
 template <bool ODD, class P, int BLK, bool D2 = false, bool PR = false, int SOLVER = 0>
 __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK> w,
                                           unsigned int* s_ctr) {
@@ -435,9 +460,8 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   // a marked cell off a retry step gets no update (it stays on the fallback
   // unless its embedding already meets the 13 constraints)
   const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
-  NewtonResult nr;
-  if constexpr (SOLVER == 1) nr = newton_chord<BLK, D2>(w, d.ph, maxit, true);
-  else nr = newton<BLK, (sizeof(P) == 4) || SOLVER == 2, D2>(w, d.ph, maxit, true);
+  int n32;
+  const NewtonResult nr = solve_cell<P, BLK, D2, SOLVER>(w, d.ph, maxit, n32);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);
   else lam[9] = lam[9] + 0.0;  // a solved state carries no embedding mark
   store_solver_state<BLK>(d, cell, w);
@@ -446,6 +470,10 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   atomicAdd(&s_ctr[CTR_UPDATES], (unsigned)nr.n_upd);
   atomicAdd(&s_ctr[CTR_HIST + min(nr.n_upd, 31)], 1u);
   atomicAdd(&s_ctr[CTR_EPS + branch], 1u);
+  if (n32) {
+    atomicAdd(&s_ctr[CTR_UPD32], (unsigned)n32);
+    atomicAdd(&s_ctr[CTR_START32], 1u);
+  }
 }
 
 // One time step over every fluid cell (even or odd AA pass).

@@ -74,7 +74,7 @@ bool params_ok(const lbm39_params* p) {
         (p->prandtl >= 0.01 && p->prandtl <= 100.0 && 2.0 / (p->gamma - 1.0) - D > 0.0)))
     return false;
   // the other root finders serve the FP64 path with the paper's Pr = 1 collision
-  if (p->root_finder < 0 || p->root_finder > 2) return false;
+  if (p->root_finder < 0 || p->root_finder > 3) return false;
   if (p->root_finder != 0 &&
       (p->precision != LBM39_FP64 || !(p->prandtl == 0.0 || p->prandtl == 1.0)))
     return false;
@@ -614,6 +614,8 @@ int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
   for (int k = 0; k < 32; ++k) s->newton_hist[k] = (int64_t)c[CTR_HIST + k];
   for (int k = 0; k < 4; ++k) s->eps_hist[k] = (int64_t)c[CTR_EPS + k];
   for (int k = 0; k < 5; ++k) s->conserved[k] = r5[k];
+  s->start32_updates = (int64_t)c[CTR_UPD32];
+  s->start32_solves = (int64_t)c[CTR_START32];
   return LBM39_OK;
 }
 

@@ -59,6 +59,8 @@ class lbm39_stats_t(ctypes.Structure):
         ("newton_hist", ctypes.c_int64 * 32),
         ("eps_hist", ctypes.c_int64 * 4),
         ("conserved", ctypes.c_double * 5),
+        ("start32_updates", ctypes.c_int64),
+        ("start32_solves", ctypes.c_int64),
     ]
 
 

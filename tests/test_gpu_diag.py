@@ -137,3 +137,21 @@ def test_precision_form_fields_are_close_to_fp64(Lat):
     em, nm = gpu_fields(Lm)
     assert np.isfinite(em).all() and (nm >= 0).all()
     np.testing.assert_allclose(em, ef, rtol=1e-3, atol=1e-6)
+
+
+@pytest.mark.parametrize("root_finder,precision", [(0, 0), (1, 0), (2, 0), (3, 0), (0, 1)])
+def test_update_counts_are_those_the_next_step_takes(Lat, root_finder, precision):
+    """The n_upd field does the next step's solve with the lattice's root finder (the precision
+    form: its single-precision start and FP32 direction): summed over the cells it equals the
+    Newton updates that step adds to the counters, and its -1 cells are the step's failures."""
+    s = inputs.box(seed=4, shape=(12, 10, 9))
+    L = Lat.from_setup(s, root_finder=root_finder, precision=precision)
+    L.step(3)
+    L.sync()
+    _, gn = gpu_fields(L)
+    s0 = L.stats()
+    L.step(1)
+    L.sync()
+    s1 = L.stats()
+    assert gn[gn >= 0].sum() == s1.newton_updates - s0.newton_updates
+    assert (gn == -1).sum() == s1.failed_cells - s0.failed_cells
