@@ -138,8 +138,10 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
   using S = Sys<D2>;
   double x[Q];
   if (from_F) {
+    if constexpr (D2) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) x[i] = F[i];
+      for (int i = 0; i < Q; ++i) x[i] = F[i];
+    }
   } else {
     double l[NM];
 #pragma unroll
@@ -152,25 +154,33 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
     else gen::exponents(l, x);
     int wide = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) wide |= exp_out_of_range(x[i]);
+    for (int i = 0; i < Q; ++i) {
+      wide |= exp_out_of_range(x[i]);
+      F[i] = x[i];
+    }
     if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
-#pragma unroll
-      for (int i = 0; i < Q; ++i) F[i] = x[i];
       exp_all_slow<BLK>(F.p);
+      if constexpr (D2) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) x[i] = F[i];
-    } else {
+        for (int i = 0; i < Q; ++i) x[i] = F[i];
+      }
+    } else if constexpr (D2) {
       static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if constexpr (D2 && zmirror(i) < i) x[i] = x[zmirror(i)];
+        if constexpr (zmirror(i) < i) x[i] = x[zmirror(i)];
         else x[i] = exp_tang_core(x[i]);
         F[i] = x[i];
       });
+    } else {
+      // one exponential at a time from the workspace: a single copy of its code
+      // (the FP64 pipe's issue rate, not the chain's latency, paces it)
+#pragma unroll 1
+      for (int i = 0; i < Q; ++i) F[i] = exp_tang_core(F[i]);
     }
   }
   double s[S::N];
   if constexpr (D2) gen::moments_s2d<double>(x, s);
-  else gen::moments_s<double>(x, s);
+  else gen::moments_s<double>(F, s);
 #pragma unroll
   for (int k = 0; k < S::N; ++k) G[k] = s[k] - m[S::idx(k)];
 }
