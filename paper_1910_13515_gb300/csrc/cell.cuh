@@ -136,14 +136,8 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
                                                  WS<BLK> m, double (&G)[Sys<D2>::N],
                                                  bool from_F) {
   using S = Sys<D2>;
-  double x[Q];
-  if (from_F) {
-    if constexpr (D2) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) x[i] = F[i];
-    }
-  } else {
-    double l[NM];
+  if (!from_F) {
+    double l[NM], x[Q];
 #pragma unroll
     for (int k = 0; k < NM; ++k) l[k] = lam[k];
     if (t != 0.0) {
@@ -160,26 +154,23 @@ __device__ __forceinline__ void eval_equilibrium(WS<BLK> lam, WS<BLK> dl, double
     }
     if (wide) {  // |e| >= 512, inf or NaN somewhere: CUDA's exp for all 39
       exp_all_slow<BLK>(F.p);
-      if constexpr (D2) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) x[i] = F[i];
-      }
-    } else if constexpr (D2) {
-      static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        if constexpr (zmirror(i) < i) x[i] = x[zmirror(i)];
-        else x[i] = exp_tang_core(x[i]);
-        F[i] = x[i];
-      });
     } else {
       // one exponential at a time from the workspace: a single copy of its code
-      // (the FP64 pipe's issue rate, not the chain's latency, paces it)
+      // (the FP64 pipe's issue rate, not the chain's latency, paces it); D2: once
+      // per z-mirror pair, then copied
 #pragma unroll 1
-      for (int i = 0; i < Q; ++i) F[i] = exp_tang_core(F[i]);
+      for (int i = 0; i < Q; ++i)
+        if (!D2 || ((kZOwn >> i) & 1ull)) F[i] = exp_tang_core(F[i]);
+      if constexpr (D2) {
+        static_for<0, Q>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          if constexpr (zmirror(i) < i) F[i] = F[zmirror(i)];
+        });
+      }
     }
   }
   double s[S::N];
-  if constexpr (D2) gen::moments_s2d<double>(x, s);
+  if constexpr (D2) gen::moments_s2d<double>(F, s);
   else gen::moments_s<double>(F, s);
 #pragma unroll
   for (int k = 0; k < S::N; ++k) G[k] = s[k] - m[S::idx(k)];

@@ -62,6 +62,15 @@ constexpr int zmirror(int i) {
   return i;
 }
 
+// Bit i set where velocity i is the first of its z-mirror pair (or its own mirror).
+constexpr unsigned long long zmirror_own_mask() {
+  unsigned long long m = 0;
+  for (int i = 0; i < Q; ++i)
+    if (zmirror(i) >= i) m |= 1ull << i;
+  return m;
+}
+constexpr unsigned long long kZOwn = zmirror_own_mask();
+
 // The constraint system solved per cell: all 13 multipliers, or (D2) the nine
 // basis functions even in xi_z.  On a lattice one cell thick in z whose
 // populations are z-mirror symmetric (u_z = 0 everywhere), the z-odd residuals
