@@ -273,8 +273,7 @@ void o39_gaussian_guess(const double *u, double T, double *lam) {
 #define N5 5               /* constraints of the fallback equilibrium */
 #define FALLBACK_MAXIT 50  /* Newton updates of the fallback from its Gaussian start */
 #define FALLBACK_TOL 1e-12
-#define RETRY_MAXIT 3      /* full-solve updates of a cell on the fallback, on a retry step */
-#define RETRY_PERIOD 8     /* such a cell retries the full solve on steps t = 0 mod this */
+#define RETRY_PERIOD 8     /* a cell on the fallback retries the full solve on steps t = 0 mod this */
 
 /* Newton-Raphson for the 13 multipliers (Sec. 3 and the Sec. 5 step table):
  * repeat { F = exp(Phi lam); G = Phi^T F - m; J = Phi^T diag(F) Phi;
@@ -753,15 +752,19 @@ int o39_newton5(const double *m, double *mu, double tol, int maxit, int *n_upd_o
  * xi_y^2 + xi_z^2), and a per-cell flag "on the fallback" is set.  On the
  * next steps a flagged cell does not repeat the full solve from scratch:
  *  - on every step t that is a multiple of RETRY_PERIOD it tries the full
- *    solve again from the embedding, with at most RETRY_MAXIT updates; a cell
+ *    solve again from the embedding, with the full Newton budget; a cell
  *    that has come back inside the cone converges and its flag is cleared;
  *  - on the other steps it takes no update (only the residual of the
  *    embedding is checked), and the fallback starts from the stored mu.
  * Cells outside the cone usually stay outside for many steps (the region is
- * carried by the flow), so this bounds the work of a cell that cannot
- * converge to a fallback solve from a close start, while a cell that has
- * re-entered the cone returns to the 13-moment equilibrium within
- * RETRY_PERIOD steps.  The rule depends on the time step alone.  If the
+ * carried by the flow), so this limits the work of a cell that cannot
+ * converge to one full attempt every RETRY_PERIOD steps and a fallback solve
+ * from a close start, while a cell that has re-entered the cone returns to
+ * the 13-moment equilibrium within RETRY_PERIOD steps.  The retry needs the
+ * full budget: from the five-multiplier embedding the full solve takes 5 to 7
+ * updates even for states well inside the cone (|u| ~ 1, T ~ 0.5), so a
+ * shorter budget keeps such cells on the fallback for good.  The rule depends
+ * on the time step alone.  If the
  * fallback fails as well, the cell keeps the multipliers the full solve left,
  * its equilibrium is evaluated there, and its flag is cleared. */
 
@@ -894,7 +897,7 @@ int o39_collide_cell(const o39_params *p, double *f, double *g, double *lam, uin
   memcpy(lam_in, lam, sizeof lam_in);
   const int flagged = *on_fb != 0;
   int maxit = p->newton_maxit;
-  if (flagged) maxit = (t % RETRY_PERIOD == 0) ? RETRY_MAXIT : 0;
+  if (flagged) maxit = (t % RETRY_PERIOD == 0) ? p->newton_maxit : 0;
   int st = solve13(p, m, lam, maxit, n_upd, F);
   if (st) {  /* counted as a failure: the cell takes the fallback this step */
     if (fallback_into(u, T, flagged ? lam_in : NULL, lam, F) == 0) {
