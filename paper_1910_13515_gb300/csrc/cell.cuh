@@ -614,11 +614,12 @@ constexpr double FALLBACK_TOL = 1e-12;
 // exponent).  A converged solve, or a fallback that fails too, clears it
 // (lam_9 + 0 turns -0 into +0 and leaves any other value alone), so a solved
 // state, even one at rest with the same shape, is never taken for one.  A
-// flagged cell retries the full solve from the embedding with RETRY_MAXIT
-// updates on the time steps that are multiples of RETRY_PERIOD, and on the
-// other steps takes no update and goes straight to the fallback, which starts
-// from the stored mu.  The schedule depends on the time step alone.
-constexpr int RETRY_MAXIT = 3;
+// flagged cell retries the full solve from the embedding with the full Newton
+// budget on the time steps that are multiples of RETRY_PERIOD (from the
+// embedding the solve takes 5-7 updates even well inside the cone, so a cell
+// that has come back inside returns there), and on the other steps takes no
+// update and goes straight to the fallback, which starts from the stored mu.
+// The schedule depends on the time step alone.
 constexpr int RETRY_PERIOD = 8;  // a power of two
 
 // F = exp(phi5 . (mu - t dl)) (t = 0: mu itself), the 13 sums s_k = sum_i F_i

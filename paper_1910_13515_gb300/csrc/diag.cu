@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(BLK) k_diag_fields(Desc d, int odd, double* ep
   targets<BLK>(M.ux, M.uy, M.uz, M.T, m);
   load_solver_state<BLK>(d, cell, w);
   const bool marked = is_fallback_embedding<BLK>(lam);
-  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
+  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t, d.ph.maxit);
   int n32;
   const NewtonResult nr = solve_cell<P, BLK, D2, SOLVER>(w, d.ph, maxit, n32);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);

@@ -412,10 +412,10 @@ __device__ __noinline__ void fallback_cell(const double* state, long long Np, lo
   }
 }
 
-// Newton budget of a cell on the fallback at time step t: RETRY_MAXIT on the
-// steps that are multiples of RETRY_PERIOD, else none.
-__device__ __forceinline__ int retry_budget(long long t) {
-  return (t & (RETRY_PERIOD - 1)) == 0 ? RETRY_MAXIT : 0;
+// Newton budget of a cell on the fallback at time step t: the full budget
+// maxit on the steps that are multiples of RETRY_PERIOD, else none.
+__device__ __forceinline__ int retry_budget(long long t, int maxit) {
+  return (t & (RETRY_PERIOD - 1)) == 0 ? maxit : 0;
 }
 
 // The constraint solve of a cell from the warm start in the workspace (F cached
@@ -459,7 +459,7 @@ __device__ __forceinline__ void step_cell(const Desc& d, long long cell, WS<BLK>
   const bool marked = is_fallback_embedding<BLK>(lam);
   // a marked cell off a retry step gets no update (it stays on the fallback
   // unless its embedding already meets the 13 constraints)
-  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t);
+  const int maxit = !marked ? d.ph.maxit : retry_budget(d.t, d.ph.maxit);
   int n32;
   const NewtonResult nr = solve_cell<P, BLK, D2, SOLVER>(w, d.ph, maxit, n32);
   if (nr.failed) fallback_cell<BLK>(d.lam, d.Np, cell, w, M.T, marked);

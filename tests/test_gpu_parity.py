@@ -320,7 +320,7 @@ def _gpu_flags(L, ncells):
 
 def test_naca_with_developing_fallback_cells_parity(Lat):
     """A small NACA0012 lattice at Ma 2.0 (u_inf = 1.67 at T_inf = 0.5): from step ~8 the flow
-    reaches states outside the 13-moment cone, and by step 40 several hundred cells are on the
+    reaches states outside the 13-moment cone, and by step 40 about 250 cells are on the
     fallback, retrying the full solve on steps 0, 8, 16, 24 and 32.  Up to step 17 the GPU
     matches the oracle to 1e-11.  Later the cells next to the cone's boundary, where the
     constraint Jacobian is nearly singular, amplify round-off: the oracle run from an initial
