@@ -288,8 +288,10 @@ def outside_blob_box():
 
 def test_cells_outside_the_cone_take_the_fallback(Lat):
     """Where the 13-moment solve fails, the cell takes the equilibrium of the five collision
-    invariants: the initial state is reproduced exactly, failures are still counted, the lattice
-    conserves mass, momentum and energy, and the GPU matches the oracle."""
+    invariants: the initial state is reproduced exactly, failures are counted as the oracle counts
+    them (the blob's cells fail at init and on steps 0-7; mixed into the flow, they are back inside
+    the cone at the retry step 8), the lattice conserves mass, momentum and energy, and the GPU
+    matches the oracle."""
     s, b = outside_blob_box()
     L = Lat.from_setup(s)
     assert L.sync() == b.sum()
@@ -298,7 +300,10 @@ def test_cells_outside_the_cone_take_the_fallback(Lat):
     assert np.abs(T - s.T).max() <= 1e-13
     c0 = np.array(L.stats().conserved)
     L.step(20)
-    assert L.sync() >= b.sum() * 21
+    st = o.init(oracle_cfg(s), s.mask, s.rho, s.u, s.T, allow_failed=True)
+    fo = st.init_failed + sum(o.step(st, 1) for _ in range(20))
+    assert fo == b.sum() * 9
+    assert L.sync() == fo
     c1 = np.array(L.stats().conserved)
     assert np.all(np.abs(c1 - c0) <= 1e-12 * np.array([c0[0]] * 4 + [c0[4]])), c1 - c0
     for n in (1, 3, 9, 17):  # across the retry steps 0, 8 and 16 of the failure policy
