@@ -3,7 +3,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload box256|box384|box128|box2d|naca|sod|poly|serve]
-                    [--precision fp64|mixed] [--sections precision,serving,airfoil|none]
+                    [--precision fp64|mixed] [--sections precision,serving,airfoil,root_finders,prandtl|none]
 
 A step is one full time step (collide + stream with the mask rules) over the whole
 lattice.  Inputs are synthetic and seeded (paper_1910_13515_gb300.inputs).  The default
@@ -11,7 +11,9 @@ line is the 3-D periodic 256^3 box in FP64 (rms Ma 0.8); the same line carries t
 parts of the metric: the precision form on the 256^3 and 384^3 boxes against the FP64
 path, a serving run (Poisson request stream, p50/p99 time-to-solution, aggregate MLUPS
 against serial stepping), the 2048x1024 NACA0012 airfoil (early window and developed
-flow) and the other root finders and stopping tolerances on the 256^3 box.  For N > 1 (torchrun, one process per GPU) every rank runs its own replica of the
+flow), the other root finders and stopping tolerances on the 256^3 box, and the
+Prandtl-number adjustment (Pr = 0.71) on the same box.  For N > 1 (torchrun, one process
+per GPU) every rank runs its own replica of the
 workload (weak scaling; the step has no exchange between replicas) and the extra sections
 are skipped.  Rank 0 prints one JSON line.
 """
@@ -82,10 +84,10 @@ FP64_FLOPS_MODEL = {
 # null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are
 # the 128^3 captures scaled by the cell count (x 8, x 27; the same per-cell work, all far
 # beyond L2).
-NCU_TRAFFIC = {"kernel_hash": "0d9755488c8f81df",
-               "gb_per_launch": {"box128/fp64": 4.759, "box256/fp64": 38.07,
-                                 "box128/mixed": 3.028, "box256/mixed": 24.22,
-                                 "box384/mixed": 81.75}}
+NCU_TRAFFIC = {"kernel_hash": "aaedb9363f8bab7e",
+               "gb_per_launch": {"box128/fp64": 4.705, "box256/fp64": 37.64,
+                                 "box128/mixed": 3.069, "box256/mixed": 24.55,
+                                 "box384/mixed": 82.86}}
 # The sources the step kernels and their launches are built from (the serving-form kernels
 # in batch.cuh are not among them).
 KERNEL_SOURCES = ("cell.cuh", "d3q39.cuh", "d3q39_gen.cuh", "expd.cuh", "kernels.cuh",
@@ -693,6 +695,40 @@ def root_finder_section(args, local, s, newton_mlups: float):
     return out
 
 
+def prandtl_section(args, local, s, pr1_mlups: float):
+    """The Prandtl-number adjustment (quasi-equilibrium collision, heat flux relaxed with
+    tau2 = 1/2 + (tau_eff - 1/2)/Pr) on the same input (the FP64 256^3 box) after the same
+    steps, at Pr = 0.71 (air) in both precisions: MLUPS, its ratio to the Pr = 1 step of the
+    same precision (FP64: the line's value) and the conservation drift."""
+    import torch
+
+    from paper_1910_13515_gb300 import lbm39 as C
+    from paper_1910_13515_gb300.lattice import Lattice
+    out = {"prandtl": 0.71}
+    fl = int((s.mask == 0).sum())
+    base = {"fp64": pr1_mlups}
+    for name, prec, pr in (("fp64", C.LBM39_FP64, 0.71), ("mixed_pr1", C.LBM39_MIXED, 1.0),
+                           ("mixed", C.LBM39_MIXED, 0.71)):
+        over = {"prandtl": pr} if pr != 1.0 else {}
+        L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}", **over)
+        c0 = L.stats().conserved
+        L.step(args.warmup)
+        _, ms, _ = timed_steps(L, args.steps, local)
+        st1 = L.stats()
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+        mlups = round(s.ncells * args.steps / (ms * 1e-3) / 1e6, 3)
+        if pr == 1.0:
+            base["mixed"] = mlups
+            continue
+        out[name] = {"mlups": mlups, "vs_prandtl_1_same_precision": round(mlups / base[name], 3),
+                     "fluid_cells": fl,
+                     "conservation_drift_rel": [float("%.2e" % v)
+                                                for v in drift_rel(c0, st1.conserved)]}
+    return out
+
+
 def airfoil_section(args, local, developed_at: int):
     """The 2048x1024 NACA0012 airfoil (Ma 1.5, Re 1e4, C = 400), FP64: the rate over the early
     window of the impulsive start (steps W..W+K) and over K steps of the developed flow from
@@ -742,9 +778,9 @@ def main():
                     help="poly workload: lattice side n of the periodic n x n x 1 lattice")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="precision form: also run the FP64 path and report L1 error, drift, speedup")
-    ap.add_argument("--sections", default="precision,serving,airfoil,root_finders",
+    ap.add_argument("--sections", default="precision,serving,airfoil,root_finders,prandtl",
                     help="FP64 256^3 box line: comma-separated extra sections to run in the same "
-                         "line (precision, serving, airfoil, root_finders), or 'none'")
+                         "line (precision, serving, airfoil, root_finders, prandtl), or 'none'")
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the serving section of the 256^3 box line")
     ap.add_argument("--serve-section-rate", type=float, default=3.0,
@@ -927,12 +963,14 @@ def main():
     suite = (args.workload == "box256" and args.precision == "fp64" and world == 1
              and args.root_finder == "newton" and args.newton_tol == 1e-12
              and args.start_at == 0 and not args.checkpoint_in)
-    serving = airfoil = solvers = None
+    serving = airfoil = solvers = prandtl = None
     if suite and "precision" in sections:
         form = precision_form_section(args, local, s, (headline_state, value))
     del headline_state
     if suite and "root_finders" in sections:
         solvers = root_finder_section(args, local, s, value)
+    if suite and "prandtl" in sections:
+        prandtl = prandtl_section(args, local, s, value)
     if suite and "airfoil" in sections:
         airfoil = airfoil_section(args, local, args.developed_at)
     if suite and "serving" in sections:
@@ -970,6 +1008,7 @@ def main():
             "serving": serving,
             "airfoil": airfoil,
             "root_finders": solvers,
+            "prandtl": prandtl,
             "kernel_hash": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)
