@@ -713,6 +713,7 @@ def prandtl_section(args, local, s, pr1_mlups: float):
         L = Lattice.from_setup(s, precision=prec, device=f"cuda:{local}", **over)
         c0 = L.stats().conserved
         L.step(args.warmup)
+        st0 = L.stats()
         _, ms, _ = timed_steps(L, args.steps, local)
         st1 = L.stats()
         L.close()
@@ -724,6 +725,8 @@ def prandtl_section(args, local, s, pr1_mlups: float):
             continue
         out[name] = {"mlups": mlups, "vs_prandtl_1_same_precision": round(mlups / base[name], 3),
                      "fluid_cells": fl,
+                     "newton_updates_per_cell": round((st1.newton_updates - st0.newton_updates)
+                                                      / (fl * args.steps), 4),
                      "conservation_drift_rel": [float("%.2e" % v)
                                                 for v in drift_rel(c0, st1.conserved)]}
     return out
