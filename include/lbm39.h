@@ -67,7 +67,7 @@ typedef enum {
   LBM39_FP64 = 0, /* populations, moments, Newton and collision in FP64 */
   LBM39_MIXED = 1 /* populations stored in FP32 as deviations from a reference
                      state, collision in FP32; moments and the constraint solve
-                     in FP64 (see lbm39_params.ref_rho / ref_T) */
+                     in FP64 (see lbm39_params.ref_rho / ref_u / ref_T) */
 } lbm39_precision;
 
 /* Run parameters (Sec. 3).  lbm39_default_params fills the defaults. */
@@ -82,7 +82,7 @@ typedef struct {
   int32_t newton_min_upd;   /* updates taken even from a converged warm start; 0 */
   int32_t init_maxit;       /* cold-start updates allowed in lbm39_init; 200 */
   int32_t precision;        /* lbm39_precision */
-  double ref_rho, ref_T;    /* LBM39_MIXED reference state (rho_bar, T_bar) */
+  double ref_rho, ref_T;    /* LBM39_MIXED reference state (rho_bar, T_bar); see ref_u */
   double rho_inf, u_inf[3], T_inf; /* far-field state held by freestream cells */
   int32_t reduce_2d;        /* 1 (default): on a lattice one cell thick in z whose initial
                                u_z and u_inf[2] are all 0, the populations stay mirror
@@ -126,6 +126,15 @@ typedef struct {
                                (the residual that decides convergence is the FP64 one);
                                FP64 path with Pr = 1 only (the precision form always
                                uses 3). */
+  double ref_u[3];          /* LBM39_MIXED: velocity of the reference state (default 0).
+                               The stored FP32 values are deviations from the 13-moment
+                               equilibrium at (ref_rho, ref_u, ref_T).  FP32 resolves a
+                               deviation to about 6e-8 of its size, so a population far
+                               below its reference value is stored coarsely: a flow that
+                               moves as a whole (a far field at Ma 1.5) keeps its
+                               populations close to the reference only if the reference
+                               moves with it.  The state must lie inside the moment cone
+                               (its equilibrium exists), else lbm39_create fails. */
 } lbm39_params;
 
 typedef struct lbm39_lattice lbm39_lattice;

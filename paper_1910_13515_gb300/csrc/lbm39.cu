@@ -5,8 +5,10 @@
 // CUDA errors to LBM39_ERR_CUDA.  Kernels are instantiated for the two
 // population storages: double (LBM39_FP64) and float deviations (LBM39_MIXED).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <mutex>
@@ -33,6 +35,17 @@ constexpr long long STAGE_CELLS = 1LL << 20;     // host staging chunk (cells)
 constexpr uint64_t CKPT_MAGIC = 0x3933424d4c424c31ull;
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// NVTX range over one call of the C ABI, named after the call, so that a
+// timeline profiler shows the host side of each call (enqueue, staging
+// copies, waits) above the kernels it launched.  Without a profiler attached
+// a push and a pop cost a few nanoseconds.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 struct AuxLayout {
   size_t lam, ctr, heq, href, fstore, partials, result, stage, total;
@@ -70,6 +83,8 @@ bool params_ok(const lbm39_params* p) {
   if (p->precision != LBM39_FP64 && p->precision != LBM39_MIXED) return false;
   if (p->reduce_2d != 0 && p->reduce_2d != 1) return false;
   if (p->precision == LBM39_MIXED && !(p->ref_rho > 0.0 && p->ref_T > 0.0)) return false;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->ref_u[a])) return false;
   if (!(p->prandtl == 0.0 || p->prandtl == 1.0 ||
         (p->prandtl >= 0.01 && p->prandtl <= 100.0 && 2.0 / (p->gamma - 1.0) - D > 0.0)))
     return false;
@@ -115,6 +130,7 @@ uint64_t params_hash(const lbm39_params* p) {
   h = fnv1a(&p->reduce_2d, sizeof p->reduce_2d, h);
   h = fnv1a(&p->prandtl, sizeof p->prandtl, h);
   h = fnv1a(&p->root_finder, sizeof p->root_finder, h);
+  h = fnv1a(p->ref_u, sizeof p->ref_u, h);
   return h;
 }
 
@@ -373,8 +389,7 @@ int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, voi
   double href[2 * Q] = {0}, heq[2 * Q] = {0};
   unsigned long long* dfail = L->ctr() + CTR_N;
   if (L->mixed) {
-    const double u0[3] = {0, 0, 0};
-    rc = state_equilibrium(d.ph, stream, p->ref_rho, u0, p->ref_T, p->init_maxit,
+    rc = state_equilibrium(d.ph, stream, p->ref_rho, p->ref_u, p->ref_T, p->init_maxit,
                            reinterpret_cast<double*>(L->aux + L->lay.href), dfail, href);
     if (rc) { delete L; return rc; }
     for (int k = 0; k < 5; ++k) d.mref[k] = 0.0;
@@ -465,6 +480,7 @@ static int init_end(lbm39_lattice* L) {
 }
 
 int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
+  const Range range("lbm39_init");
   if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
   int rc = init_begin(L);
   if (rc) return rc;
@@ -474,6 +490,7 @@ int lbm39_init(lbm39_lattice* L, const double* rho, const double* u, const doubl
 }
 
 int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const double* T) {
+  const Range range("lbm39_init_host");
   if (!L || !rho || !u || !T) return LBM39_ERR_ARG;
   int rc = init_begin(L);
   if (rc) return rc;
@@ -503,6 +520,7 @@ int lbm39_init_host(lbm39_lattice* L, const double* rho, const double* u, const 
 }
 
 int lbm39_step(lbm39_lattice* L, int64_t nsteps) {
+  const Range range("lbm39_step");
   if (!L || nsteps < 0) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -515,6 +533,7 @@ int lbm39_step(lbm39_lattice* L, int64_t nsteps) {
 }
 
 int lbm39_sync(lbm39_lattice* L, int64_t timeout_us, int64_t* failed_cells) {
+  const Range range("lbm39_sync");
   if (!L) return LBM39_ERR_ARG;
   cudaEvent_t ev;
   CUDA_OK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -550,12 +569,14 @@ static int read_range(lbm39_lattice* L, double* rho, double* u, long long us, do
 }
 
 int lbm39_read(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
+  const Range range("lbm39_read");
   if (!L) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   return read_range(L, rho, u, L->N, T, p, 0, L->N);
 }
 
 int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double* p) {
+  const Range range("lbm39_read_host");
   if (!L) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   const size_t nb = sizeof(double) * L->N;
@@ -591,6 +612,7 @@ int lbm39_read_host(lbm39_lattice* L, double* rho, double* u, double* T, double*
 }
 
 int lbm39_stats(lbm39_lattice* L, lbm39_stats_t* s) {
+  const Range range("lbm39_stats");
   if (!L || !s) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   double* partials = reinterpret_cast<double*>(L->aux + L->lay.partials);
@@ -625,6 +647,7 @@ size_t lbm39_checkpoint_bytes(const lbm39_lattice* L) {
 }
 
 int lbm39_save(lbm39_lattice* L, void* buf) {
+  const Range range("lbm39_save");
   if (!L || !buf) return LBM39_ERR_ARG;
   if (!L->initialized) return LBM39_ERR_STATE;
   uint64_t hdr[32] = {0};
@@ -648,6 +671,7 @@ int lbm39_save(lbm39_lattice* L, void* buf) {
 }
 
 int lbm39_load(lbm39_lattice* L, const void* buf) {
+  const Range range("lbm39_load");
   if (!L || !buf) return LBM39_ERR_ARG;
   uint64_t hdr[32];
   const char* b = static_cast<const char*>(buf);
@@ -826,6 +850,7 @@ int lbm39_batch_create(int32_t max_lattices, int64_t max_cells, int32_t precisio
 
 int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_t* t_end,
                     int32_t n) {
+  const Range range("lbm39_batch_set");
   if (!B || n < 0 || n > B->maxlat || (n > 0 && (!lattices || !t_end))) return LBM39_ERR_ARG;
   long long cells = 0;
   for (int j = 0; j < n; ++j) {
@@ -871,6 +896,7 @@ int lbm39_batch_set(lbm39_batch* B, lbm39_lattice* const* lattices, const int64_
 }
 
 int lbm39_batch_run(lbm39_batch* B, int64_t nsteps) {
+  const Range range("lbm39_batch_run");
   if (!B || nsteps < 0) return LBM39_ERR_ARG;
   if (B->hE.empty() || nsteps == 0) return LBM39_OK;
   int64_t done = 0;

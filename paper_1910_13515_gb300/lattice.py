@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import lbm39 as C
-from .inputs import Setup
+from .inputs import M_FREE, Setup
 
 
 def velocities():
@@ -23,6 +23,11 @@ def velocities():
 
 
 def params_from_setup(s: Setup, precision: int = C.LBM39_FP64, **over) -> C.lbm39_params:
+    """Run parameters of a setup.  The precision form of a lattice with freestream cells
+    stores its populations as deviations from the far-field equilibrium (ref_rho, ref_u,
+    ref_T = rho_inf, u_inf, T_inf), so that the flow that moves with the far field is stored
+    finely; other lattices keep the library's rest reference (1, 0, 0.5).  Keyword
+    arguments override any field."""
     p = C.lbm39_default_params(s.nx, s.ny, s.nz)
     for a in range(3):
         p.periodic[a] = int(s.periodic[a])
@@ -33,6 +38,11 @@ def params_from_setup(s: Setup, precision: int = C.LBM39_FP64, **over) -> C.lbm3
     p.rho_inf = s.rho_inf
     p.T_inf = s.T_inf
     p.precision = precision
+    if precision == C.LBM39_MIXED and s.mask is not None and \
+            bool((np.asarray(s.mask) == M_FREE).any()):
+        p.ref_rho, p.ref_T = s.rho_inf, s.T_inf
+        for a in range(3):
+            p.ref_u[a] = float(s.u_inf[a])
     for k, v in over.items():
         setattr(p, k, v)
     return p

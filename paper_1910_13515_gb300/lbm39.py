@@ -47,6 +47,7 @@ class lbm39_params(ctypes.Structure):
         ("reduce_2d", ctypes.c_int32),
         ("prandtl", ctypes.c_double),
         ("root_finder", ctypes.c_int32),
+        ("ref_u", ctypes.c_double * 3),
     ]
 
 

@@ -65,6 +65,28 @@ def test_default_params_and_sizes(C):
     assert aux_b >= 52 * 8 * Np
 
 
+def test_params_layout_matches_the_header(C):
+    """lbm39_default_params writes exactly the binding's lbm39_params: nothing past its end
+    (the C struct is no larger), and the last field (ref_u) at the binding's offset."""
+    import ctypes
+    n = ctypes.sizeof(C.lbm39_params)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    C._lib.lbm39_default_params(ctypes.cast(buf, ctypes.POINTER(C.lbm39_params)), 8, 8, 8)
+    assert bytes(buf[n:]) == b"\xab" * 64
+    p = C.lbm39_params.from_buffer(buf)
+    assert list(p.ref_u) == [0.0, 0.0, 0.0] and p.ref_T == 0.5 and p.prandtl == 1.0
+    assert p.root_finder == 0 and (p.nx, p.ny, p.nz) == (8, 8, 8)
+
+
+def test_nonfinite_reference_velocity_rejected(C):
+    p = C.lbm39_default_params(8, 8, 8)
+    p.precision = C.LBM39_MIXED
+    p.ref_u[0] = float("nan")
+    assert C.lbm39_query_bytes(p)[0] == C.LBM39_ERR_ARG
+    p.ref_u[0] = 1.0
+    assert C.lbm39_query_bytes(p)[0] == 0
+
+
 @pytest.mark.parametrize("field,value", [("nx", 0), ("gamma", 1.0), ("tau", 0.4),
                                          ("newton_tol", 0.0), ("newton_maxit", 0),
                                          ("precision", 7)])

@@ -44,16 +44,26 @@ def test_mixed_box_l1_error_vs_oracle(mod, shape, seed, steps):
     assert max(err) <= 1e-4, err
 
 
-def test_mixed_naca_small_l1_error_vs_oracle(mod):
-    """Impulsive start of Ma 1.5 flow on a 24-cell chord: during the first steps some cells
-    sit on the thresholds of the piecewise-constant alpha(eps) (Eq. alpha), and the FP32-stored
-    state (1e-7 away from FP64) flips a branch in a handful of them; each flip changes tau_eff
-    by 5-35% in that cell.  Before the first flip (steps 0-2) the forms agree to ~1e-8; after
-    100 steps the L1 difference is ~6e-4.  The 1e-4 bar belongs to the precision-form
-    configs (the periodic boxes, tested above); this case is held to 2e-3."""
+@pytest.mark.parametrize("reference,bar", [("far field", 1e-4), ("rest", 2e-3)])
+def test_mixed_naca_small_l1_error_vs_oracle(mod, reference, bar):
+    """Impulsive start of Ma 1.5 flow on a 24-cell chord, against the FP64 oracle.
+
+    Far-field reference (the default for a lattice with freestream cells): the stored FP32
+    values are deviations from the far-field equilibrium, zero in the undisturbed flow and of
+    the size of the populations themselves near the airfoil, so FP32 resolves them to ~6e-8
+    of the population.  Held to the precision form's 1e-4 after 100 steps (storage rounding
+    emulated on the oracle gives 5.9e-5).
+
+    Rest reference (ref_u = 0): at Ma 1.5 the smallest populations lie four to five orders of
+    magnitude below their reference values, so their deviations are stored to ~1e-3 of the
+    populations; that moves eps of cells near a threshold of Eq. (alpha) across it, and each
+    flip changes tau_eff by 5-35% in that cell.  Before the first flip (steps 0-2) the forms
+    agree to ~1e-8; after 100 steps the L1 difference is ~6e-4, held to 2e-3."""
     C, Lattice = mod
     s = inputs.naca(nx=96, ny=48, chord=24, x_le=24)
-    L = Lattice.from_setup(s, precision=C.LBM39_MIXED)
+    over = {} if reference == "far field" else {"ref_u": (0.0, 0.0, 0.0)}
+    L = Lattice.from_setup(s, precision=C.LBM39_MIXED, **over)
+    assert list(L.params.ref_u) == ([s.u_inf[0], 0.0, 0.0] if not over else [0.0, 0.0, 0.0])
     L.step(2)
     assert L.sync() == 0
     st, fo = run_oracle(s, 2)
@@ -62,7 +72,8 @@ def test_mixed_naca_small_l1_error_vs_oracle(mod):
     assert L.sync() == 0
     o.step(st, 98)
     err = l1_rel(L.read_numpy(), o.macros(st), s.mask)
-    assert max(err) <= 2e-3, err
+    print(f"precision form, {reference} reference: L1 after 100 steps {err}")
+    assert max(err) <= bar, err
 
 
 def test_mixed_sod_l1_error_vs_oracle(mod):
