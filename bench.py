@@ -84,7 +84,7 @@ FP64_FLOPS_MODEL = {
 # null once that code differs (profiles/ has the captures).  The 256^3 and 384^3 figures are
 # the 128^3 captures scaled by the cell count (x 8, x 27; the same per-cell work, all far
 # beyond L2).
-NCU_TRAFFIC = {"kernel_hash": "aaedb9363f8bab7e",
+NCU_TRAFFIC = {"kernel_hash": "98f81eefb40860d3",
                "gb_per_launch": {"box128/fp64": 4.705, "box256/fp64": 37.64,
                                  "box128/mixed": 3.069, "box256/mixed": 24.55,
                                  "box384/mixed": 82.86}}

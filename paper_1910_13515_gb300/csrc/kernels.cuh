@@ -561,6 +561,17 @@ __global__ void __launch_bounds__(BLK) k_state_equilibrium(Phys ph, double rho, 
   if (nr.failed) atomicAdd(failed, 1ull);
 }
 
+// A population reversed by the bounce-back: the stored value v of population
+// `from` becomes population `to`.  FP64 storage holds the populations
+// themselves; the precision form holds deviations from the reference
+// populations, which differ between the two directions unless the reference
+// is at rest, so the value is re-referenced: (v + h_ref,from) - h_ref,to.
+template <class P>
+__device__ __forceinline__ P reversed(const Desc& d, P v, int from, int to) {
+  if constexpr (sizeof(P) == 8) return v;
+  else return __double2float_rn((double)v + (__ldg(d.href + from) - __ldg(d.href + to)));
+}
+
 // After an even pass: freestream cells hold the far-field post-collision
 // populations and outflow cells a copy of the cell with x clamped into
 // [3, nx-4], both in the reversed (post-collision) layout the odd pass reads.
@@ -575,9 +586,10 @@ __device__ __forceinline__ void bounce_even_cell(const Desc& d, long long s) {
   for (int i = 0; i < Q; ++i) {
     const long long x = nb.at(kCX[i], kCY[i], kCZ[i]);
     if (d.mask[x] != MASK_FLUID) continue;
-    const int o = opp(i);
-    pop[(long long)o * d.Np + s] = pop[(long long)i * d.Np + x];
-    pop[(long long)(Q + o) * d.Np + s] = pop[(long long)(Q + i) * d.Np + x];
+    const int o = opp(i);  // slot i of x holds population o of x; it returns as population i
+    pop[(long long)o * d.Np + s] = reversed<P>(d, pop[(long long)i * d.Np + x], o, i);
+    pop[(long long)(Q + o) * d.Np + s] =
+        reversed<P>(d, pop[(long long)(Q + i) * d.Np + x], Q + o, Q + i);
   }
 }
 
@@ -592,9 +604,10 @@ __device__ __forceinline__ void bounce_odd_cell(const Desc& d, long long s) {
   for (int i = 0; i < Q; ++i) {
     const long long x = nb.at(-kCX[i], -kCY[i], -kCZ[i]);
     if (d.mask[x] != MASK_FLUID) continue;
-    const int o = opp(i);
-    pop[(long long)o * d.Np + x] = pop[(long long)i * d.Np + s];
-    pop[(long long)(Q + o) * d.Np + x] = pop[(long long)(Q + i) * d.Np + s];
+    const int o = opp(i);  // population i of x returns as its population o
+    pop[(long long)o * d.Np + x] = reversed<P>(d, pop[(long long)i * d.Np + s], i, o);
+    pop[(long long)(Q + o) * d.Np + x] =
+        reversed<P>(d, pop[(long long)(Q + i) * d.Np + s], Q + i, Q + o);
   }
 }
 
