@@ -387,7 +387,7 @@ def serving_section(args, local, n_requests: int, rate_hz: float, seed: int = 0)
     serial = cs / (time.perf_counter() - t0) / 1e6
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "budget_gib": 4,
             "cell_steps": rep.cell_steps, "max_resident": rep.max_resident,
-            "rounds": rep.rounds,
+            "rounds": rep.rounds, "requests_with_fallback_cells": len(rep.failed),
             "p50_ms": round(rep.p50_ms, 2), "p99_ms": round(rep.p99_ms, 2),
             "aggregate_mlups": round(rep.mlups, 3), "serial_mlups": round(serial, 3),
             "speedup_vs_serial": round(rep.mlups / serial, 3),

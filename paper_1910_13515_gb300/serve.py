@@ -13,7 +13,9 @@ memory for the next requests, so work that arrives while others run overlaps
 with them on the device.  A request withdrawn by its client (Request.cancel_s)
 is dropped if it is still waiting, or released at the next run boundary
 (between steps) if it is resident; its memory goes to the next requests and the
-report lists it with the steps it completed.
+report lists it with the steps it completed.  A request whose flow leaves the
+13-moment cone is served like the others (its cells take the five-invariant
+fallback); the report lists its fallback cell-steps (Report.failed).
 
 Scheduler holds the policy and is independent of the GPU (a test drives it with a
 fake backend); GpuBackend does the device work through the C ABI.
@@ -50,6 +52,7 @@ class Report:
     max_resident: int = 0
     rounds: int = 0
     cancelled: dict = field(default_factory=dict)   # rid -> steps completed before withdrawal
+    failed: dict = field(default_factory=dict)      # rid -> cell-steps that took the fallback
 
     @property
     def p50_ms(self) -> float:
@@ -94,6 +97,8 @@ class Scheduler:
         rounds = 0
         busy = getattr(self.be, "busy", None)   # asynchronous backends only
         wait = getattr(self.be, "wait", None)
+        failed_of = getattr(self.be, "failed", None)
+        failed: dict = {}
 
         def arrivals(now):
             while pending and pending[0].arrival_s <= now:
@@ -157,6 +162,9 @@ class Scheduler:
             if finished:
                 for j in finished:
                     j.result = self.be.read(j.handle)
+                    nf = failed_of(j.handle) if failed_of is not None else 0
+                    if nf:
+                        failed[j.req.rid] = nf
                     j.t_done = self.clock() - t0
                     self.be.release(j.handle)
                     used -= j.bytes
@@ -170,7 +178,7 @@ class Scheduler:
         lat = [j.t_done - j.req.arrival_s for j in done.values()]
         cells = sum(j.req.setup.ncells * j.steps for j in done.values())
         return Report(lat, wall, cells, {rid: j.result for rid, j in done.items()}, max_res,
-                      rounds, cancelled)
+                      rounds, cancelled, failed)
 
 
 def _withdrawn(job: Job, now: float) -> bool:
@@ -236,11 +244,16 @@ class GpuBackend:
             self.done_ev.synchronize()
 
     def read(self, L):
+        """The finished lattice's rho, u, T, p.  Cells whose constraint solve failed took the
+        five-invariant fallback (a valid, conservative state): failed(L) reports how many
+        cell-steps did, so one request leaving the moment cone does not stop the others."""
         self.wait()
-        failed = L.sync()
-        if failed:
-            raise RuntimeError(f"{failed} Newton failures in a served lattice")
+        L.served_failed = L.sync()
         return L.read_numpy()
+
+    def failed(self, L) -> int:
+        """Cell-steps of the lattice that took the fallback equilibrium (after read)."""
+        return int(getattr(L, "served_failed", 0))
 
     def release(self, L):
         self.wait()

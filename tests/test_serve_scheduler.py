@@ -205,3 +205,26 @@ def test_arrivals_during_a_run_are_set_up_meanwhile_and_join_the_next_run():
     assert be.max_bytes_seen <= budget and not be.live
     assert be.admitted_while_busy > 0
     assert rep.cell_steps == sum(r.setup.ncells * r.setup.steps for r in reqs)
+
+
+class FailingBackend(FakeBackend):
+    """A backend whose lattice for one request reports fallback cell-steps."""
+
+    def __init__(self, clock, failing_cells):
+        super().__init__(clock)
+        self.failing_cells = failing_cells
+
+    def failed(self, h):
+        return 17 if self.live[h].ncells == self.failing_cells else 0
+
+
+def test_newton_failures_are_reported_per_request_and_do_not_stop_the_stream():
+    clock = FakeClock()
+    reqs = make_requests()
+    odd = reqs[3].setup.ncells
+    be = FailingBackend(clock, odd)
+    rep = Scheduler(be, 3 * 32 * 32 * 100, max_resident=4, chunk_steps=7, clock=clock,
+                    sleep=clock.sleep).run(reqs)
+    assert sorted(rep.results) == [r.rid for r in reqs]
+    assert rep.failed == {r.rid: 17 for r in reqs if r.setup.ncells == odd}
+    assert rep.failed
