@@ -157,8 +157,8 @@ typedef struct {
 
 /* Fills *p with defaults for an nx*ny*nz fully periodic FP64 lattice
  * (gamma 1.4, tau 0.6, sensor on, tol 1e-12, maxit 30, min_upd 0,
- * init_maxit 200, ref (1, 0.5), far field (1, 0, 0.5), reduce_2d 1, Pr 1,
- * Newton root finder). */
+ * init_maxit 200, reference (rho, u, T) = (1, 0, 0.5), far field (1, 0, 0.5),
+ * reduce_2d 1, Pr 1, Newton root finder). */
 void lbm39_default_params(lbm39_params* p, int32_t nx, int32_t ny, int32_t nz);
 
 /* The compiled D3Q39 velocity set (Sec. 3: (0,0,0), (1,0,0)_FS, (+-1,+-1,+-1),
@@ -180,7 +180,10 @@ int lbm39_query_bytes(const lbm39_params* p, size_t* pop_bytes, size_t* aux_byte
  * mask_dev: device mask of N cells or NULL (all fluid; needs every axis
  * periodic).  The mask is validated (LBM39_ERR_MASK) and must stay unchanged
  * and alive while the lattice exists.  cuda_stream: a cudaStream_t or NULL
- * for the legacy default stream.  *out receives the handle. */
+ * for the legacy default stream.  *out receives the handle.  The far-field
+ * state (with freestream cells) and, for LBM39_MIXED, the reference state
+ * must have a 13-moment equilibrium: if their cold-start solve fails, no
+ * lattice is created and LBM39_ERR_NEWTON is returned. */
 int lbm39_create(const lbm39_params* p, const int32_t* vel, const double* w, void* pop_buf,
                  void* aux_buf, const uint8_t* mask_dev, void* cuda_stream,
                  lbm39_lattice** out);
